@@ -1,0 +1,205 @@
+/*
+ * tmotif: exact co-mining of delta-temporal motifs on a B300 (sm_103a).
+ *
+ * The library loads a temporal graph onto the GPU, builds a Motif-Group Tree
+ * (MG-Tree) from a motif set, and returns one exact 64-bit count per motif.
+ *
+ * Problem statement (Section 2, "A Temporal Graph", "A delta-Temporal
+ * Motif", "Temporal Motif Mining"): edges are ordered by (t, input index),
+ * which fixes the edge id (eid).  A match of motif ((u_1,v_1),...,(u_m,v_m))
+ * with window delta is a tuple of eids e_1 < ... < e_m with
+ * t(e_m) - t(e_1) <= delta and one injective map f from motif vertices to
+ * graph vertices with f(u_i) = src(e_i), f(v_i) = dst(e_i).  A motif's count
+ * is its number of matches (no division by automorphisms).
+ *
+ * Conventions for every call:
+ *   - return value 0 (TM_OK) on success, a negative TM_E* code otherwise;
+ *     tm_last_error() then gives a message for the calling thread;
+ *   - inputs are copied; the caller keeps ownership of every pointer passed;
+ *   - handles (tm_graph, tm_tree) are immutable after creation and may be
+ *     used from several streams at once; free them once, after all work that
+ *     uses them has finished;
+ *   - "stream" is a cudaStream_t (NULL = legacy default stream).
+ */
+#ifndef TMOTIF_H
+#define TMOTIF_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------ error codes */
+#define TM_OK 0
+#define TM_EINVAL (-1)        /* invalid argument or input data */
+#define TM_ENOMEM (-2)        /* device or host allocation failed */
+#define TM_ECUDA (-3)         /* a CUDA call failed */
+#define TM_ETIMEOUT (-4)      /* a bounded device-side wait ran out */
+#define TM_EUNSUPPORTED (-5)  /* motif beyond TM_MAX_EDGES / TM_MAX_VERTICES */
+
+/* ------------------------------------------------------------ limits */
+#define TM_MAX_EDGES 8        /* edges per motif */
+#define TM_MAX_VERTICES 8     /* vertices per motif */
+#define TM_MAX_DELTAS 64      /* distinct windows in one tree */
+#define TM_MAX_NODES 4096     /* nodes in one tree */
+
+typedef struct tm_graph tm_graph;   /* opaque, library-owned */
+typedef struct tm_tree tm_tree;     /* opaque, library-owned */
+
+/* ------------------------------------------------------------ graph */
+#define TM_INPUT_DEVICE 0x1u  /* src/dst/t point to device memory */
+#define TM_PRESORTED 0x2u     /* input is already in (t, index) order; checked */
+
+/*
+ * Load a temporal graph (Section 2; the time-sorted adjacency of Section 4.1,
+ * step 2 of the workflow).
+ *   src, dst: n_edges int32 vertex ids in [0, n_nodes)
+ *   t:        n_edges int64 timestamps (any order unless TM_PRESORTED)
+ *   flags:    TM_INPUT_DEVICE, TM_PRESORTED
+ * The library orders the edges by (t, input index), then builds on the device
+ * the per-vertex out- and in-lists in edge-id order and a (src, dst) pair
+ * index.  Self-loops are accepted (no motif can match them).  Errors:
+ * TM_EINVAL for n_edges < 0 or >= 2^31, n_nodes < 1, an id out of range,
+ * TM_PRESORTED input that is not sorted; TM_ENOMEM; TM_ECUDA.
+ * The call synchronises `stream` before returning.
+ */
+int tm_graph_load(const int32_t *src, const int32_t *dst, const int64_t *t, int64_t n_edges,
+                  int32_t n_nodes, uint32_t flags, void *stream, tm_graph **out);
+
+typedef struct {
+    int64_t n_edges;
+    int32_t n_nodes;
+    int32_t reserved;
+    int64_t n_pairs;          /* distinct (src, dst) pairs */
+    int64_t max_out_degree;
+    int64_t max_in_degree;
+    int64_t device_bytes;     /* device memory held by the handle */
+} tm_graph_info;
+
+int tm_graph_get_info(const tm_graph *g, tm_graph_info *info);
+
+/* Copy the edge list in edge-id order to host arrays (n_edges each; any may be NULL). */
+int tm_graph_edges(const tm_graph *g, int32_t *src, int32_t *dst, int64_t *t);
+
+int tm_graph_free(tm_graph *g);
+
+/* ------------------------------------------------------------ MG-Tree */
+/*
+ * Build the Motif-Group Tree of a motif set (Section 4.2, Algorithm 2;
+ * node composition <C_N, Children(N), Q_N> of Appendix A).
+ *   motif_uv:  2 * sum(m_i) int8 vertex labels, edge j of motif i at
+ *              motif_uv[2*(motif_off[i]+j)] (source), [.. + 1] (destination)
+ *   motif_off: n_motifs + 1 offsets (in edges) into motif_uv
+ *   delta:     n_motifs int64 windows (>= 0); motifs may carry different
+ *              windows, each counted with its own
+ * Labels are canonicalised (order of first appearance); motifs equal after
+ * that share one node and keep separate counts.  The tree is the radix trie
+ * of canonical edge sequences: one node per branch point or motif end, the
+ * root at the longest common prefix.  Errors: TM_EINVAL for an empty motif,
+ * a self-loop edge (u == v), a negative label or delta; TM_EUNSUPPORTED for
+ * more than TM_MAX_EDGES edges or TM_MAX_VERTICES vertices in a motif, more
+ * than TM_MAX_DELTAS distinct windows or TM_MAX_NODES nodes.
+ */
+int tm_tree_build(const int8_t *motif_uv, const int32_t *motif_off, int32_t n_motifs,
+                  const int64_t *delta, tm_tree **out);
+
+typedef struct {
+    int32_t n_motifs;
+    int32_t n_nodes;
+    int32_t n_leaves;
+    int32_t depth;            /* edges of the longest motif */
+    int32_t n_deltas;         /* distinct windows */
+    int32_t max_vertices;
+    double similarity;        /* SM of Section 6: 1 - sum(|E_N|-|E_parent|) / sum |E_M| */
+} tm_tree_info;
+
+int tm_tree_get_info(const tm_tree *tr, tm_tree_info *info);
+
+/* One node of the tree in preorder (root = 0), for inspection. */
+typedef struct {
+    int32_t parent;           /* -1 for the root */
+    int32_t n_edges;          /* |C_N| */
+    int32_t n_children;
+    int32_t n_refs;           /* motifs whose canonical form equals C_N */
+    int8_t u[TM_MAX_EDGES];   /* C_N, canonical labels */
+    int8_t v[TM_MAX_EDGES];
+} tm_tree_node;
+
+int tm_tree_get_node(const tm_tree *tr, int32_t index, tm_tree_node *node);
+
+int tm_tree_free(tm_tree *tr);
+
+/* ------------------------------------------------------------ counting */
+/* mode bits */
+#define TM_COMINE 0x0u        /* walk the MG-Tree (Algorithm 3) */
+#define TM_PERMOTIF 0x1u      /* one chain per distinct motif, one launch each (Algorithm 1) */
+#define TM_LEAF_SCAN 0x10u    /* count a leaf's last edge by scanning its window only */
+#define TM_SCHED_DYNAMIC 0x100u /* persistent launch, heavy subtrees split across warps */
+
+/* flags */
+#define TM_ROOTS_DEVICE 0x1u  /* roots points to device memory */
+#define TM_COUNTS_DEVICE 0x2u /* counts points to device memory (no sync) */
+
+/* per-root work counters, TM_WORK_FIELDS int64 per root */
+#define TM_WORK_CANDIDATES 0  /* adjacency entries scanned in windows */
+#define TM_WORK_EXPANSIONS 1  /* candidate lists opened */
+#define TM_WORK_PROBES 2      /* binary-search and hash probes */
+#define TM_WORK_LEAF_EVALS 3  /* leaf edges counted by range arithmetic */
+#define TM_WORK_FIELDS 4
+
+typedef struct {
+    uint32_t mode;            /* TM_COMINE or TM_PERMOTIF, | TM_LEAF_SCAN, | TM_SCHED_DYNAMIC */
+    uint32_t flags;           /* TM_ROOTS_DEVICE, TM_COUNTS_DEVICE */
+    const int32_t *roots;     /* root edge ids (any order, may repeat); NULL: range below */
+    int64_t n_roots;
+    int64_t root_lo;          /* with roots == NULL: roots are eids [root_lo, root_hi) */
+    int64_t root_hi;          /*   root_hi <= 0 means n_edges */
+    int64_t *per_root_counts; /* device, [n_roots][n_motifs], or NULL; overwritten */
+    int64_t *per_root_work;   /* device, [n_roots][TM_WORK_FIELDS], or NULL; overwritten */
+    int32_t ctas_per_sm;      /* 0: library default */
+    int32_t reserved;
+} tm_count_args;
+
+typedef struct {
+    int64_t n_roots;
+    int64_t candidates;       /* totals of the work counters above */
+    int64_t expansions;
+    int64_t probes;
+    int64_t leaf_evals;
+    int64_t algo_bytes;       /* bytes the method reads: 16 per root + 8 per candidate
+                                 + 8 per list probe + 16 per hash probe + 4 per pair probe */
+    int64_t tasks_split;      /* subtrees handed to other warps (TM_SCHED_DYNAMIC) */
+    int64_t launches;         /* kernel launches issued by the call */
+    double kernel_ms;         /* device time of the mining launches */
+} tm_run_stats;
+
+/*
+ * Count every motif of `tr` in `g` (Algorithm 3 when mode has TM_COMINE,
+ * Algorithm 1 per motif with TM_PERMOTIF); both give the same counts.
+ *   counts: n_motifs int64, caller-owned, host memory (the call then
+ *           synchronises `stream`) or device memory with TM_COUNTS_DEVICE;
+ *           overwritten with the counts of the selected roots
+ *   stats:  optional; when non-NULL the call collects work counters and
+ *           synchronises `stream`
+ * Roots: every edge is a candidate for the first motif edge (Algorithm 1,
+ * first call); counts are additive over roots, so a root list or range
+ * yields the counts of matches whose first edge is in it.  Errors:
+ * TM_EINVAL (NULL handle, root out of range, n_roots < 0); TM_ETIMEOUT if a
+ * bounded device wait of TM_SCHED_DYNAMIC ran out (counts are then invalid);
+ * TM_ECUDA; TM_ENOMEM.
+ */
+int tm_count(const tm_graph *g, const tm_tree *tr, const tm_count_args *args, int64_t *counts,
+             tm_run_stats *stats, void *stream);
+
+/* Message describing the last error on the calling thread ("" if none). */
+const char *tm_last_error(void);
+
+/* Library version string. */
+const char *tm_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TMOTIF_H */

@@ -47,7 +47,8 @@ def _load():
         lib = ctypes.CDLL(_LIB)
         P = ctypes.c_void_p
         i64, i32 = ctypes.c_int64, ctypes.c_int32
-        lib.oracle_count_motif.argtypes = [P, P, P, i64, i32, P, P, ctypes.c_int, i64, P, i64, i64, P, P, P]
+        lib.oracle_count_motif.argtypes = [P, P, P, i64, i32, P, P, ctypes.c_int, i64, P, i64, i64,
+                                           ctypes.c_int, P, P, P]
         lib.oracle_count_motif.restype = ctypes.c_int
         lib.oracle_comine.argtypes = [P, P, P, i64, i32, ctypes.c_int, P, P, P, P, P, P, P,
                                       ctypes.c_int, i64, P, i64, i64, P, P, P]
@@ -73,12 +74,17 @@ def _graph(src, dst, t, n_nodes):
 
 
 def count_motif(src, dst, t, motif: Sequence, delta: int, roots=None, n_nodes=None,
-                max_work: int = 0, per_root: bool = False, work: bool = False):
+                max_work: int = 0, per_root: bool = False, work: bool = False,
+                root_budget: int = 0):
     """Algorithm 1: count one motif.  Returns total (and per-root / work arrays).
 
     ``max_work`` bounds the candidates examined; when it is exceeded the
-    result is ``None`` (the count would be incomplete).
+    result is ``None`` (the count would be incomplete).  With ``root_budget``
+    the bound applies per root instead: a root past it gets per-root count -1
+    and is left out of the total.
     """
+    if root_budget:
+        max_work = int(root_budget)
     src, dst, t, V = _graph(src, dst, t, n_nodes)
     m = mgtree.canonical(motif)
     mu = np.array([e[0] for e in m], np.int8)
@@ -89,8 +95,8 @@ def count_motif(src, dst, t, motif: Sequence, delta: int, roots=None, n_nodes=No
     wk = np.zeros(nr, np.int64) if work else None
     tot = ctypes.c_int64(0)
     rc = _load().oracle_count_motif(_p(src), _p(dst), _p(t), len(src), V, _p(mu), _p(mv), len(m),
-                                    int(delta), _p(r), nr, int(max_work), ctypes.byref(tot),
-                                    _p(pr), _p(wk))
+                                    int(delta), _p(r), nr, int(max_work), 1 if root_budget else 0,
+                                    ctypes.byref(tot), _p(pr), _p(wk))
     if rc < 0:
         raise ValueError("oracle rejected the motif or delta")
     total = None if rc == 1 else int(tot.value)

@@ -66,6 +66,7 @@ typedef struct {
     int64_t t_limit;    /* t_first + delta, saturated */
     int64_t work;       /* candidates examined */
     int64_t max_work;   /* abort when exceeded (<= 0: unlimited) */
+    double deadline;    /* CLOCK_MONOTONIC seconds; abort after it (<= 0: none) */
     int aborted;
     /* motif (Algorithm 1) */
     int m;
@@ -79,6 +80,12 @@ typedef struct {
     const int32_t *ref_off, *ref_idx; /* Q_N: query indices counted at N */
     int64_t *counts;              /* per query */
 } og_ctx;
+
+static double now_s(void) {
+    struct timespec ts;
+    clock_gettime(CLOCK_MONOTONIC, &ts);
+    return (double)ts.tv_sec + 1e-9 * (double)ts.tv_nsec;
+}
 
 static int64_t sat_add(int64_t a, int64_t b) {
     if (b > 0 && a > INT64_MAX - b) return INT64_MAX;
@@ -155,6 +162,7 @@ static void match_one_edge(og_ctx *c, int node, int em, int uM, int vM, descend_
         if (te > c->t_limit) break;                       /* every later edge fails too */
         c->work++;
         if (c->max_work > 0 && c->work > c->max_work) { c->aborted = 1; return; }
+        if (c->deadline > 0 && (c->work & 0xFFFFF) == 0 && now_s() > c->deadline) { c->aborted = 1; return; }
         /* temporal constraints (order: strictly later edge id, R1; window, R2) */
         if (e <= last || te > c->t_limit) continue;
         int32_t eu = g->src[e], ev = g->dst[e];
@@ -209,12 +217,14 @@ static void free_ctx(og_ctx *c) { free(c->g2m); free(c->incnt); free(c); }
  *   roots:  edge ids allowed as the first motif edge (NULL: all edges)
  *   per_root: optional output, count for each root
  *   work_out: optional, candidates examined per root
+ *   root_budget: when non-zero, max_work applies to each root separately and
+ *     a root that exceeds it gets per_root = -1 (excluded from *total)
  * Returns 0, or 1 when max_work was exceeded (outputs then incomplete),
  * or -1 for invalid input.
  */
 int oracle_count_motif(const int32_t *src, const int32_t *dst, const int64_t *t, int64_t E, int32_t V,
                        const int8_t *mu, const int8_t *mv, int m, int64_t delta,
-                       const int32_t *roots, int64_t n_roots, int64_t max_work,
+                       const int32_t *roots, int64_t n_roots, int64_t max_work, int root_budget,
                        int64_t *total, int64_t *per_root, int64_t *work_out) {
     if (m < 1 || m > OR_MAXE || delta < 0) return -1;
     for (int i = 0; i < m; i++)
@@ -235,7 +245,19 @@ int oracle_count_motif(const int32_t *src, const int32_t *dst, const int64_t *t,
         }
         if (per_root) per_root[i] = c->count - before;
         if (work_out) work_out[i] = c->work - w0;
+        if (c->aborted && root_budget) {
+            /* this root alone ran past the budget: mark it and go on */
+            if (per_root) per_root[i] = -1;
+            c->count = before;
+            c->aborted = 0;
+            c->work = 0;
+            /* undo the mappings left by the interrupted recursion */
+            for (int32_t v = 0; v < g.V; v++) { c->g2m[v] = -1; c->incnt[v] = 0; }
+            for (int q = 0; q < OR_MAXV; q++) c->m2g[q] = -1;
+            continue;
+        }
         if (c->aborted) { rc = 1; break; }
+        if (root_budget) c->work = 0;
     }
     sum = c->count;
     if (total) *total = sum;
@@ -307,9 +329,10 @@ int oracle_comine(const int32_t *src, const int32_t *dst, const int64_t *t, int6
 /*
  * Algorithm 1 over roots spread across threads with dynamic scheduling (the
  * paper's CPU task manager, Section 4.5), for the timed CPU baseline only.
- * Each thread owns a private context.  Returns 0, or 1 when the time limit
- * (seconds, <= 0: none) ran out, with *n_done roots finished (a prefix is not
- * guaranteed: per_root entries of unfinished roots are -1).
+ * Each thread owns a private context.  Stops once time_limit seconds (> 0)
+ * have passed, also inside a root; *n_done roots were finished, and
+ * per_root is -1 for every other root.  Returns 0, 1 when the limit was
+ * reached, -1 for invalid input.
  */
 int oracle_count_motif_mt(const int32_t *src, const int32_t *dst, const int64_t *t, int64_t E, int32_t V,
                           const int8_t *mu, const int8_t *mv, int m, int64_t delta,
@@ -318,27 +341,26 @@ int oracle_count_motif_mt(const int32_t *src, const int32_t *dst, const int64_t 
     if (m < 1 || m > OR_MAXE || delta < 0) return -1;
     og_graph g = {E, V, src, dst, t, 0, 0, 0, 0};
     build_adj(&g);
-    struct timespec ts0; clock_gettime(CLOCK_MONOTONIC, &ts0);
-    int64_t done = 0; volatile int timed_out = 0;
+    double t0 = now_s();
+    int64_t done = 0;
+    volatile int timed_out = 0;
     for (int64_t i = 0; i < n_roots; i++) per_root[i] = -1;
 #pragma omp parallel num_threads(n_threads) reduction(+:done)
     {
         og_ctx *c = new_ctx(&g);
         c->m = m; c->mu = mu; c->mv = mv;
+        c->deadline = time_limit > 0 ? t0 + time_limit : 0;
 #pragma omp for schedule(dynamic, 1)
         for (int64_t i = 0; i < n_roots; i++) {
-            if (timed_out) continue;
-            if (time_limit > 0) {
-                struct timespec ts; clock_gettime(CLOCK_MONOTONIC, &ts);
-                double el = (double)(ts.tv_sec - ts0.tv_sec) + 1e-9 * (double)(ts.tv_nsec - ts0.tv_nsec);
-                if (el > time_limit) { timed_out = 1; continue; }
-            }
+            if (timed_out || c->aborted) continue;
+            if (time_limit > 0 && now_s() > t0 + time_limit) { timed_out = 1; continue; }
             int32_t r = roots[i];
             int64_t before = c->count;
             if (start_root(c, r, mu[0], mv[0], delta)) {
                 match_edge(c, 0, 1);
                 roll_back(c, src[r], dst[r]);
             }
+            if (c->aborted) { timed_out = 1; continue; }   /* interrupted inside this root */
             per_root[i] = c->count - before;
             done++;
         }

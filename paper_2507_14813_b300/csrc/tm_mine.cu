@@ -1,0 +1,698 @@
+// Co-mining kernel: exact counts of every motif of an MG-Tree.
+//
+// Algorithm 3 (CoMatchEdge) walked by one warp per root edge.  Every edge is
+// a candidate for the first motif edge (Algorithm 1, first call); each later
+// motif edge draws candidates from the out-list of the mapped source or the
+// in-list of the mapped destination (reading 4), restricted to edge ids in
+// (previous match, last edge within the window] (temporal constraints,
+// readings 1-2) and filtered for structure with full injectivity (reading 3).
+// When C_N of a node is complete the node's queries are counted and its
+// children are mined from the same partial match, in table order.
+//
+// Per level the warp loads 32 adjacency entries (one coalesced 8-byte load
+// per lane), evaluates the predicate branch-free, and takes the ballot.
+// Surviving candidates are kept in a per-warp shared-memory stack and
+// descended one at a time, depth first.
+//
+// Leaf edges.  The last edge of a leaf node is never descended.  In scan
+// mode the warp counts its survivors with popc per chunk (the paper's scan).
+// Otherwise every survivor of the level above counts its own leaf edge in
+// parallel (one lane per survivor) by exact window arithmetic:
+//     |candidates| = |list in (last, hi]| - sum over mapped w of |pair (x,w) in (last, hi]|
+// using binary searches on the time-sorted list and the (src, dst) pair
+// index; lanes with a short window scan it instead.  Both give the count the
+// scan gives.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "tm_internal.h"
+
+namespace tmo {
+namespace {
+
+constexpr int kWarps = 8;                 // warps per CTA
+constexpr int kThreads = kWarps * 32;
+constexpr int kSmemCounters = 2048;       // per-CTA counters kept in shared memory up to this many
+constexpr int kLaneScanMax = 24;          // leaf windows up to this size are scanned by the lane
+
+enum : int8_t { kListOut = 0, kListIn = 1, kListGlobal = 2 };
+
+struct Params {
+    DevGraph g;
+    DevTree tr;
+    const int32_t *roots;
+    int64_t n_roots;
+    int64_t root_lo;
+    unsigned long long *counts;       // n_counters
+    int64_t *per_root_counts;         // [n_roots][n_counters] or null
+    int64_t *per_root_work;           // [n_roots][TM_WORK_FIELDS] or null
+    unsigned long long *cursor;       // root cursor (zeroed before launch)
+    unsigned long long *stats;        // kStatFields totals or null
+    int32_t chunk;                    // roots claimed per cursor step
+    int32_t smem_counters;            // 1: per-CTA counters in shared memory
+};
+
+enum { kStCand = 0, kStExp, kStListProbe, kStHashProbe, kStPairProbe, kStLeaf, kStRoots, kStatFields };
+
+struct WarpState {
+    int2 cand[kMaxE][32];
+    int64_t pos[kMaxE];       // next chunk start (absolute index into the list array)
+    int64_t end[kMaxE];       // list end
+    int64_t cbase[kMaxE];     // start of the chunk held in cand[k]
+    uint32_t mask[kMaxE];     // survivors of the held chunk not yet descended
+    int32_t lvert[kMaxE];     // list vertex (out/in lists)
+    int32_t eid[kMaxE];       // matched edge id per level
+    int64_t mpos[kMaxE];      // list position of the matched candidate
+    int16_t node[kMaxE];
+    int16_t sib_end[kMaxE];
+    int8_t ltype[kMaxE];
+    int32_t m2g[kMaxV];
+    int32_t ehi[TM_MAX_DELTAS];
+};
+
+struct Work {
+    unsigned long long v[kStatFields];
+};
+
+__device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long x) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    return x;
+}
+
+__device__ __forceinline__ int64_t sat_add(int64_t a, int64_t b) {
+    return (b > 0 && a > INT64_MAX - b) ? INT64_MAX : a + b;
+}
+
+// last edge id e >= r with t[e] <= limit (t[r] <= limit holds); serial, per lane
+__device__ int32_t window_end(const int64_t *__restrict__ t, int64_t E, int32_t r, int64_t limit, unsigned long long &probes) {
+    int64_t lo = r, step = 1;          // t[lo] <= limit
+    int64_t hi = E;                    // t[hi] > limit or hi == E
+    while (true) {                     // gallop
+        int64_t q = lo + step;
+        if (q >= E) break;
+        probes++;
+        if (__ldg(t + q) <= limit) { lo = q; step <<= 1; } else { hi = q; break; }
+    }
+    while (hi - lo > 1) {
+        int64_t mid = lo + (hi - lo) / 2;
+        probes++;
+        if (__ldg(t + mid) <= limit) lo = mid; else hi = mid;
+    }
+    return (int32_t)lo;
+}
+
+// first position in adj[lo, hi) whose edge id exceeds key (hi if none); per lane
+__device__ __forceinline__ int64_t lane_upper(const int2 *__restrict__ adj, int64_t lo, int64_t hi, int32_t key,
+                                              unsigned long long &probes) {
+    while (lo < hi) {
+        int64_t mid = lo + ((hi - lo) >> 1);
+        probes++;
+        if (__ldg(&adj[mid].y) <= key) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ int64_t lane_upper_e(const int32_t *__restrict__ a, int64_t lo, int64_t hi, int32_t key,
+                                                unsigned long long &probes) {
+    while (lo < hi) {
+        int64_t mid = lo + ((hi - lo) >> 1);
+        probes++;
+        if (__ldg(a + mid) <= key) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
+// first position in adj[lo, hi) whose edge id exceeds key; warp-cooperative
+__device__ int64_t warp_upper(const int2 *__restrict__ adj, int64_t lo, int64_t hi, int32_t key, int lane,
+                              unsigned long long &probes) {
+    while (hi - lo > 32) {
+        int64_t step = (hi - lo + 31) >> 5;
+        int64_t q = lo + (int64_t)(lane + 1) * step - 1;
+        if (q > hi - 1) q = hi - 1;
+        bool gt = __ldg(&adj[q].y) > key;
+        probes += 1;
+        uint32_t b = __ballot_sync(0xffffffffu, gt);
+        if (b == 0) return hi;
+        int f = __ffs(b) - 1;
+        int64_t qf = __shfl_sync(0xffffffffu, q, f);
+        int64_t qp = __shfl_sync(0xffffffffu, q, f > 0 ? f - 1 : 0);
+        lo = f > 0 ? qp + 1 : lo;
+        hi = qf;                        // answer <= qf; hi is returned if nothing in [lo, qf) qualifies
+    }
+    int64_t q = lo + lane;
+    bool gt = q < hi && __ldg(&adj[q].y) > key;
+    probes += q < hi;
+    uint32_t b = __ballot_sync(0xffffffffu, gt);
+    return b ? lo + (__ffs(b) - 1) : hi;
+}
+
+// |edges x -> w with lo < eid <= hi|
+__device__ int64_t pair_count(const DevGraph &g, int32_t x, int32_t w, int32_t lo, int32_t hi,
+                              unsigned long long &hprobes, unsigned long long &pprobes) {
+    if (hi <= lo) return 0;
+    unsigned long long key = ((unsigned long long)(uint32_t)x << 32) | (uint32_t)w;
+    uint64_t h = pair_hash(key) & g.pair_mask;
+    while (true) {
+        hprobes++;
+        ulonglong2 e = __ldg(&g.pair_tab[h]);
+        if (e.x == key) {
+            int64_t st = (int64_t)(e.y & 0xffffffffull);
+            int64_t len = (int64_t)(e.y >> 32);
+            const int32_t *run = g.pair_eid + st;
+            if (len <= 16) {
+                int64_t c = 0;
+                for (int64_t i = 0; i < len; i++) {
+                    int32_t v = __ldg(run + i);
+                    c += (v > lo) & (v <= hi);
+                }
+                pprobes += len;
+                return c;
+            }
+            int64_t a = lane_upper_e(run, 0, len, lo, pprobes);
+            int64_t b = lane_upper_e(run, a, len, hi, pprobes);
+            return b - a;
+        }
+        if (e.x == kEmptyKey) return 0;
+        h = (h + 1) & g.pair_mask;
+    }
+}
+
+template <bool kStats>
+struct Miner {
+    const Params &p;
+    WarpState &ws;
+    unsigned long long *s_cnt;
+    int lane;
+    Work w;
+    int64_t ri;                        // root index (for per-root outputs)
+
+    __device__ Miner(const Params &pp, WarpState &s, unsigned long long *c, int l)
+        : p(pp), ws(s), s_cnt(c), lane(l) {
+        for (int i = 0; i < kStatFields; i++) w.v[i] = 0;
+    }
+
+    __device__ __forceinline__ void add_count(int32_t counter, unsigned long long c) {
+        // called by one lane
+        if (c == 0) return;
+        if (p.smem_counters) atomicAdd(&s_cnt[counter], c);
+        else atomicAdd(&p.counts[counter], c);
+        if (p.per_root_counts)
+            atomicAdd((unsigned long long *)&p.per_root_counts[ri * p.tr.n_counters + counter], c);
+    }
+
+    // value of motif label l for a lane whose level-k candidate maps (uk -> cs, vk -> cd)
+    __device__ __forceinline__ int32_t lab(int l, int uk, int vk, int32_t cs, int32_t cd) const {
+        return l == uk ? cs : (l == vk ? cd : ws.m2g[l]);
+    }
+
+    // Count the leaf edge `lv` of node L for one lane (candidate at level lv - 1
+    // with endpoints cs -> cd, edge id last), for every ref of L.
+    __device__ void leaf_eval(const DevNode &L, int lv, int uk, int vk, int32_t cs, int32_t cd, int32_t last) {
+        const DevGraph &g = p.g;
+        const int u = L.eu[lv], v = L.ev[lv];
+        const int nv = L.nvb[lv];                       // mapped labels before the leaf edge
+        const bool um = u < nv, vm = v < nv;
+        int32_t img[kMaxV];
+#pragma unroll
+        for (int l = 0; l < kMaxV; l++) img[l] = (l < nv) ? lab(l, uk, vk, cs, cd) : -1;
+        unsigned long long hp = 0, pp = 0, lp = 0;
+        for (int ri2 = 0; ri2 < L.n_ref; ri2++) {
+            const DevRef ref = p.tr.refs[L.ref_begin + ri2];
+            const int32_t hi = ws.ehi[ref.delta];
+            int64_t c = 0;
+            if (um && vm) {
+                c = pair_count(g, img[u], img[v], last, hi, hp, pp);
+            } else {
+                const bool out = um;
+                const int32_t x = out ? img[u] : img[v];
+                const int2 *adj = out ? g.out_adj : g.in_adj;
+                const int64_t *off = out ? g.out_off : g.in_off;
+                int64_t b0 = __ldg(off + x), b1 = __ldg(off + x + 1);
+                int64_t a = lane_upper(adj, b0, b1, last, lp);
+                int64_t b = lane_upper(adj, a, b1, hi, lp);
+                if (b - a <= kLaneScanMax) {
+                    for (int64_t i = a; i < b; i++) {
+                        int32_t y = __ldg(&adj[i].x);
+                        bool bad = false;
+#pragma unroll
+                        for (int l = 0; l < kMaxV; l++) bad |= (l < nv) & (y == img[l]);
+                        c += !bad;
+                    }
+                    if (kStats) w.v[kStCand] += (unsigned long long)(b - a);
+                } else {
+                    c = b - a;
+#pragma unroll
+                    for (int l = 0; l < kMaxV; l++) {
+                        if (l < nv) c -= out ? pair_count(g, x, img[l], last, hi, hp, pp)
+                                             : pair_count(g, img[l], x, last, hi, hp, pp);
+                    }
+                }
+            }
+            ref_total_[ri2 & 7] += (unsigned long long)c;   // accumulated per ref slot, flushed by caller
+        }
+        if (kStats) {
+            w.v[kStHashProbe] += hp;
+            w.v[kStPairProbe] += pp;
+            w.v[kStListProbe] += lp;
+            w.v[kStLeaf] += 1;
+        }
+    }
+    unsigned long long ref_total_[8];
+
+    // Evaluate leaf node L's last level for all survivor lanes S at level k.
+    __device__ void leaf_batch(const DevNode &L, int k, uint32_t S, int uk, int vk, int32_t cs, int32_t cd,
+                               int32_t last) {
+        // refs beyond 8 are handled in groups of 8
+        for (int base = 0; base < L.n_ref; base += 8) {
+            DevNode Lg = L;
+            Lg.ref_begin = (int16_t)(L.ref_begin + base);
+            Lg.n_ref = (int16_t)min(8, L.n_ref - base);
+#pragma unroll
+            for (int i = 0; i < 8; i++) ref_total_[i] = 0;
+            if ((S >> lane) & 1u) leaf_eval(Lg, k + 1, uk, vk, cs, cd, last);
+            for (int i = 0; i < Lg.n_ref; i++) {
+                unsigned long long tot = warp_sum_u64(ref_total_[i]);
+                if (lane == 0) add_count(p.tr.refs[Lg.ref_begin + i].counter, tot);
+            }
+        }
+    }
+
+    // Chunk-level work for survivors S of level k of node N; returns the
+    // mask of survivors to descend.
+    __device__ uint32_t survivors(int k, const DevNode &N, uint32_t S, int2 c) {
+        if (S == 0) return 0;
+        const int uk = N.eu[k], vk = N.ev[k];
+        // endpoints of this lane's candidate
+        int32_t cs, cd;
+        const int8_t lt = ws.ltype[k];
+        if (lt == kListOut) { cs = ws.lvert[k]; cd = c.x; }
+        else if (lt == kListIn) { cs = c.x; cd = ws.lvert[k]; }
+        else { cs = ((S >> lane) & 1u) ? __ldg(p.g.src + c.y) : 0; cd = ((S >> lane) & 1u) ? __ldg(p.g.dst + c.y) : 0; }
+        const bool complete = (k == N.k_end - 1);
+        if (complete && N.n_ref > 0) {                     // Q_N counted (Algorithm 3)
+            for (int i = 0; i < N.n_ref; i++) {
+                const DevRef ref = p.tr.refs[N.ref_begin + i];
+                uint32_t in = __ballot_sync(0xffffffffu, c.y <= ws.ehi[ref.delta]) & S;
+                if (lane == 0) add_count(ref.counter, (unsigned long long)__popc(in));
+            }
+        }
+        if (complete && N.n_par > 0) {
+            for (int ci = 0; ci < N.n_par; ci++) {
+                const DevNode L = p.tr.nodes[N.child_begin + N.n_seq + ci];
+                uint32_t S2 = __ballot_sync(0xffffffffu, c.y < ws.ehi[L.dmax]) & S;
+                if (S2) leaf_batch(L, k, S2, uk, vk, cs, cd, c.y);
+            }
+        }
+        const bool par_self = (N.flags & kNodeParLeaf) && (k == N.k_end - 2);
+        if (par_self) {
+            uint32_t S2 = __ballot_sync(0xffffffffu, c.y < ws.ehi[N.dmax]) & S;
+            if (S2) leaf_batch(N, k, S2, uk, vk, cs, cd, c.y);
+        }
+        bool seq = complete ? (N.n_seq > 0) : !par_self;
+        return seq ? S : 0u;
+    }
+
+    // Open level k for node `node` (siblings up to sib_end).
+    __device__ void open(int k, int node, int sib_end) {
+        const DevNode N = p.tr.nodes[node];
+        const int u = N.eu[k], v = N.ev[k], nv = N.nvb[k];
+        const bool um = u < nv, vm = v < nv;
+        const int32_t last = ws.eid[k - 1];
+        int8_t lt;
+        int32_t x = 0;
+        int64_t b0 = 0, b1 = 0;
+        if (um && vm) {
+            int32_t xu = ws.m2g[u], xv = ws.m2g[v];
+            int64_t du = __ldg(p.g.out_off + xu + 1) - __ldg(p.g.out_off + xu);
+            int64_t dv = __ldg(p.g.in_off + xv + 1) - __ldg(p.g.in_off + xv);
+            if (du <= dv) { lt = kListOut; x = xu; } else { lt = kListIn; x = xv; }
+        } else if (um) { lt = kListOut; x = ws.m2g[u]; }
+        else if (vm) { lt = kListIn; x = ws.m2g[v]; }
+        else { lt = kListGlobal; }
+        int64_t start;
+        if (lt == kListGlobal) {
+            b0 = (int64_t)last + 1;
+            b1 = (int64_t)ws.ehi[N.dmax] + 1;
+            start = b0;
+        } else {
+            const int64_t *off = lt == kListOut ? p.g.out_off : p.g.in_off;
+            b0 = __ldg(off + x);
+            b1 = __ldg(off + x + 1);
+            if (ws.ltype[k - 1] == lt && ws.lvert[k - 1] == x) {
+                start = ws.mpos[k - 1] + 1;             // same list as the level above
+            } else if (b1 - b0 <= 32) {
+                start = b0;                             // the chunk mask drops eids <= last
+            } else {
+                const int2 *adj = lt == kListOut ? p.g.out_adj : p.g.in_adj;
+                start = warp_upper(adj, b0, b1, last, lane, w.v[kStListProbe]);
+            }
+        }
+        __syncwarp();
+        if (lane == 0) {
+            ws.node[k] = (int16_t)node;
+            ws.sib_end[k] = (int16_t)sib_end;
+            ws.ltype[k] = lt;
+            ws.lvert[k] = x;
+            ws.pos[k] = start;
+            ws.end[k] = b1;
+            ws.mask[k] = 0;
+        }
+        __syncwarp();
+        if (kStats && lane == 0) w.v[kStExp]++;
+    }
+
+    // Load and filter the next chunk of level k; returns survivors to descend.
+    __device__ void load_chunk(int k) {
+        const DevNode N = p.tr.nodes[ws.node[k]];
+        const int8_t lt = ws.ltype[k];
+        const int64_t base = ws.pos[k];
+        const int64_t i = base + lane;
+        const int64_t end = ws.end[k];
+        const int32_t last = ws.eid[k - 1];
+        const int32_t hi = ws.ehi[N.dmax];
+        bool valid = i < end;
+        int2 c = make_int2(0, 0);
+        if (valid) {
+            if (lt == kListOut) c = __ldg(&p.g.out_adj[i]);
+            else if (lt == kListIn) c = __ldg(&p.g.in_adj[i]);
+            else c = make_int2(0, (int32_t)i);
+        }
+        const bool inwin = c.y <= hi;
+        const uint32_t outw = __ballot_sync(0xffffffffu, valid && !inwin);
+        valid = valid && inwin && c.y > last;
+        // structural predicate (reading 3), branch-free over the mapped labels
+        const int u = N.eu[k], v = N.ev[k], nv = N.nvb[k];
+        const bool um = u < nv, vm = v < nv;
+        bool ok;
+        if (lt == kListGlobal) {
+            int32_t s = valid ? __ldg(p.g.src + c.y) : 0, d = valid ? __ldg(p.g.dst + c.y) : 0;
+            bool bad = (s == d);
+#pragma unroll
+            for (int l = 0; l < kMaxV; l++) bad |= (l < nv) & ((s == ws.m2g[l]) | (d == ws.m2g[l]));
+            ok = !bad;
+        } else if (um && vm) {
+            ok = c.x == (lt == kListOut ? ws.m2g[v] : ws.m2g[u]);
+        } else {
+            bool bad = false;
+#pragma unroll
+            for (int l = 0; l < kMaxV; l++) bad |= (l < nv) & (c.x == ws.m2g[l]);
+            ok = !bad;
+        }
+        const uint32_t S = __ballot_sync(0xffffffffu, valid && ok);
+        const uint32_t VB = __ballot_sync(0xffffffffu, valid);
+        if (kStats && lane == 0) w.v[kStCand] += (unsigned long long)__popc(VB);
+        ws.cand[k][lane] = c;
+        uint32_t D = survivors(k, N, S, c);
+        __syncwarp();
+        if (lane == 0) {
+            ws.cbase[k] = base;
+            ws.pos[k] = outw ? end : base + 32;
+            ws.mask[k] = D;
+        }
+        __syncwarp();
+    }
+
+    __device__ void root(int32_t r) {
+        const DevGraph &g = p.g;
+        const int32_t a = __ldg(g.src + r), b = __ldg(g.dst + r);
+        if (a == b) return;                             // injective map needs a != b
+        const int64_t tr0 = __ldg(g.t + r);
+        for (int j = lane; j < p.tr.n_deltas; j += 32) {
+            unsigned long long pr = 0;
+            ws.ehi[j] = window_end(g.t, g.E, r, sat_add(tr0, __ldg(p.tr.deltas + j)), pr);
+            if (kStats) w.v[kStListProbe] += pr;
+        }
+        if (lane == 0) {
+            ws.ltype[0] = kListGlobal;
+            ws.lvert[0] = -1;
+            ws.node[0] = 0;
+            ws.sib_end[0] = 1;
+            ws.pos[0] = 0;
+            ws.end[0] = 0;
+            ws.cbase[0] = r;
+        }
+        __syncwarp();
+        // level 0: the root edge as a one-candidate chunk on lane 0
+        const DevNode N0 = p.tr.nodes[0];
+        int2 c = make_int2(lane == 0 ? b : 0, lane == 0 ? r : 0);
+        ws.cand[0][lane] = c;
+        uint32_t D = survivors(0, N0, 1u, c);
+        __syncwarp();
+        if (lane == 0) ws.mask[0] = D;
+        __syncwarp();
+
+        int k = 0;
+        while (k >= 0) {
+            uint32_t m = ws.mask[k];
+            if (m) {
+                const int j = __ffs(m) - 1;
+                const int2 cj = ws.cand[k][j];
+                const DevNode N = p.tr.nodes[ws.node[k]];
+                const int8_t lt = ws.ltype[k];
+                int32_t cs, cd;
+                if (lt == kListOut) { cs = ws.lvert[k]; cd = cj.x; }
+                else if (lt == kListIn) { cs = cj.x; cd = ws.lvert[k]; }
+                else { cs = __ldg(g.src + cj.y); cd = __ldg(g.dst + cj.y); }
+                __syncwarp();
+                if (lane == 0) {
+                    ws.mask[k] = m & (m - 1);
+                    ws.eid[k] = cj.y;
+                    ws.mpos[k] = ws.cbase[k] + j;
+                    ws.m2g[N.eu[k]] = cs;
+                    ws.m2g[N.ev[k]] = cd;
+                }
+                __syncwarp();
+                if (k == N.k_end - 1) {
+                    if (N.n_seq > 0) {
+                        open(k + 1, N.child_begin, N.child_begin + N.n_seq);
+                        k++;
+                    }
+                } else {
+                    open(k + 1, ws.node[k], ws.node[k] + 1);
+                    k++;
+                }
+                continue;
+            }
+            if (ws.pos[k] < ws.end[k]) {
+                load_chunk(k);
+                continue;
+            }
+            if (ws.node[k] + 1 < ws.sib_end[k]) {        // next sibling from the same partial match
+                open(k, ws.node[k] + 1, ws.sib_end[k]);
+                continue;
+            }
+            k--;
+        }
+    }
+};
+
+template <bool kStats>
+__global__ void __launch_bounds__(kThreads) k_mine(Params p) {
+    extern __shared__ unsigned long long s_cnt[];
+    __shared__ WarpState s_ws[kWarps];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (p.smem_counters)
+        for (int i = threadIdx.x; i < p.tr.n_counters; i += blockDim.x) s_cnt[i] = 0;
+    __syncthreads();
+    Miner<kStats> M(p, s_ws[warp], s_cnt, lane);
+    while (true) {
+        unsigned long long first = 0;
+        if (lane == 0) first = atomicAdd(p.cursor, (unsigned long long)p.chunk);
+        first = __shfl_sync(0xffffffffu, first, 0);
+        if (first >= (unsigned long long)p.n_roots) break;
+        const int64_t last = min((int64_t)first + p.chunk, p.n_roots);
+        for (int64_t ri = (int64_t)first; ri < last; ri++) {
+            M.ri = ri;
+            const int32_t r = p.roots ? __ldg(p.roots + ri) : (int32_t)(p.root_lo + ri);
+            Work before = M.w;
+            M.root(r);
+            if (kStats) {
+                if (lane == 0) M.w.v[kStRoots]++;
+                if (p.per_root_work) {
+                    // lane partials are summed; each lane holds its own probe counts
+                    unsigned long long d[4];
+                    d[0] = warp_sum_u64(M.w.v[kStCand] - before.v[kStCand]);
+                    d[1] = warp_sum_u64(M.w.v[kStExp] - before.v[kStExp]);
+                    d[2] = warp_sum_u64(M.w.v[kStListProbe] + M.w.v[kStHashProbe] + M.w.v[kStPairProbe] -
+                                        before.v[kStListProbe] - before.v[kStHashProbe] - before.v[kStPairProbe]);
+                    d[3] = warp_sum_u64(M.w.v[kStLeaf] - before.v[kStLeaf]);
+                    if (lane == 0)
+                        for (int f = 0; f < 4; f++) p.per_root_work[ri * TM_WORK_FIELDS + f] = (int64_t)d[f];
+                }
+            }
+        }
+    }
+    if (kStats) {
+        for (int f = 0; f < kStatFields; f++) {
+            unsigned long long s = warp_sum_u64(M.w.v[f]);
+            if (lane == 0 && s) atomicAdd(&p.stats[f], s);
+        }
+    }
+    __syncthreads();
+    if (p.smem_counters)
+        for (int i = threadIdx.x; i < p.tr.n_counters; i += blockDim.x)
+            if (s_cnt[i]) atomicAdd(&p.counts[i], s_cnt[i]);
+}
+
+__global__ void k_to_i64(const unsigned long long *a, int64_t *b, int n) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) b[i] = (int64_t)a[i];
+}
+
+struct LaunchShape {
+    int blocks;
+    int smem;
+};
+
+}  // namespace
+
+int mine(const tm_graph *g, const tm_tree *tr, const tm_count_args *args, int64_t *counts,
+         tm_run_stats *stats, cudaStream_t s) {
+    const int n_motifs = tr->h.n_motifs;
+    const bool comine = (args->mode & TM_PERMOTIF) == 0;
+    const bool par = (args->mode & TM_LEAF_SCAN) == 0;
+    const bool want_stats = stats != nullptr;
+    int64_t n_roots;
+    if (args->roots) {
+        n_roots = args->n_roots;
+    } else {
+        int64_t hi = args->root_hi > 0 ? args->root_hi : g->d.E;
+        if (args->root_lo < 0 || hi > g->d.E || args->root_lo > hi) {
+            set_error("tm_count: root range outside [0, n_edges]");
+            return TM_EINVAL;
+        }
+        n_roots = hi - args->root_lo;
+    }
+    if (n_roots < 0) { set_error("tm_count: n_roots < 0"); return TM_EINVAL; }
+
+    // device scratch: counters, root cursors (one per launch), stats
+    const int n_launch = comine ? 1 : (int)tr->chains.size();
+    size_t bytes = sizeof(unsigned long long) * ((size_t)n_motifs + (size_t)n_launch + kStatFields);
+    void *scratch = nullptr;
+    TM_CUDA_TRY(cudaMallocAsync(&scratch, bytes, s));
+    unsigned long long *d_cnt = (unsigned long long *)scratch;
+    unsigned long long *d_cur = d_cnt + n_motifs;
+    unsigned long long *d_st = d_cur + n_launch;
+    int rc = TM_OK;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    auto fail = [&](int code) {
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+        cudaFreeAsync(scratch, s);
+        return code;
+    };
+    if (cudaMemsetAsync(scratch, 0, bytes, s) != cudaSuccess) { set_error("tm_count: memset"); return fail(TM_ECUDA); }
+
+    // validate a host root list up front; device lists are checked by the caller's contract
+    if (args->roots && !(args->flags & TM_ROOTS_DEVICE)) {
+        for (int64_t i = 0; i < n_roots; i++)
+            if (args->roots[i] < 0 || args->roots[i] >= g->d.E) {
+                set_error("tm_count: root edge id out of range");
+                return fail(TM_EINVAL);
+            }
+    }
+    const int32_t *d_roots = args->roots;
+    void *roots_copy = nullptr;
+    if (args->roots && !(args->flags & TM_ROOTS_DEVICE) && n_roots > 0) {
+        if (cudaMallocAsync(&roots_copy, sizeof(int32_t) * n_roots, s) != cudaSuccess) {
+            set_error("tm_count: root list allocation");
+            return fail(TM_ENOMEM);
+        }
+        cudaMemcpyAsync(roots_copy, args->roots, sizeof(int32_t) * n_roots, cudaMemcpyHostToDevice, s);
+        d_roots = (const int32_t *)roots_copy;
+    }
+    if (args->per_root_counts && n_roots > 0)
+        cudaMemsetAsync(args->per_root_counts, 0, sizeof(int64_t) * n_roots * n_motifs, s);
+    if (args->per_root_work && n_roots > 0)
+        cudaMemsetAsync(args->per_root_work, 0, sizeof(int64_t) * n_roots * TM_WORK_FIELDS, s);
+
+    int dev = 0, n_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+    const bool smem_cnt = n_motifs <= kSmemCounters;
+    const int dyn_smem = smem_cnt ? (int)(sizeof(unsigned long long) * n_motifs) : 0;
+    auto kern = want_stats ? k_mine<true> : k_mine<false>;
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, dyn_smem);
+    if (args->ctas_per_sm > 0) per_sm = std::min(per_sm, (int)args->ctas_per_sm);
+    per_sm = std::max(per_sm, 1);
+    const int blocks = n_sm * per_sm;
+    const int64_t warps_total = (int64_t)blocks * kWarps;
+    int32_t chunk = (int32_t)std::max<int64_t>(1, std::min<int64_t>(16, n_roots / (warps_total * 64)));
+
+    if (want_stats) {
+        cudaEventCreate(&e0);
+        cudaEventCreate(&e1);
+        cudaEventRecord(e0, s);
+    }
+    int64_t launches = 0;
+    for (int L = 0; L < n_launch && n_roots > 0; L++) {
+        DevTree dt;
+        rc = tree_device(tr, comine ? 0 : 1 + L, par, s, &dt);
+        if (rc != TM_OK) return fail(rc);
+        Params prm;
+        prm.g = g->d;
+        prm.tr = dt;
+        prm.roots = d_roots;
+        prm.n_roots = n_roots;
+        prm.root_lo = args->roots ? 0 : args->root_lo;
+        prm.counts = d_cnt;
+        prm.per_root_counts = args->per_root_counts;
+        prm.per_root_work = (L == 0) ? args->per_root_work : nullptr;
+        prm.cursor = d_cur + L;
+        prm.stats = d_st;
+        prm.chunk = chunk;
+        prm.smem_counters = smem_cnt ? 1 : 0;
+        kern<<<blocks, kThreads, dyn_smem, s>>>(prm);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) {
+            set_error(std::string("tm_count: launch: ") + cudaGetErrorString(e));
+            return fail(TM_ECUDA);
+        }
+        launches++;
+    }
+    if (want_stats) cudaEventRecord(e1, s);
+
+    if (args->flags & TM_COUNTS_DEVICE) {
+        k_to_i64<<<(n_motifs + 255) / 256, 256, 0, s>>>(d_cnt, counts, n_motifs);
+    } else {
+        std::vector<unsigned long long> h(n_motifs);
+        cudaMemcpyAsync(h.data(), d_cnt, sizeof(unsigned long long) * n_motifs, cudaMemcpyDeviceToHost, s);
+        cudaError_t e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) {
+            set_error(std::string("tm_count: ") + cudaGetErrorString(e));
+            return fail(TM_ECUDA);
+        }
+        for (int i = 0; i < n_motifs; i++) counts[i] = (int64_t)h[i];
+    }
+    if (want_stats) {
+        unsigned long long hs[kStatFields];
+        cudaMemcpyAsync(hs, d_st, sizeof(hs), cudaMemcpyDeviceToHost, s);
+        cudaError_t e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) {
+            set_error(std::string("tm_count: ") + cudaGetErrorString(e));
+            return fail(TM_ECUDA);
+        }
+        float ms = 0;
+        cudaEventElapsedTime(&ms, e0, e1);
+        memset(stats, 0, sizeof(*stats));
+        stats->n_roots = (int64_t)hs[kStRoots];
+        stats->candidates = (int64_t)hs[kStCand];
+        stats->expansions = (int64_t)hs[kStExp];
+        stats->probes = (int64_t)(hs[kStListProbe] + hs[kStHashProbe] + hs[kStPairProbe]);
+        stats->leaf_evals = (int64_t)hs[kStLeaf];
+        stats->algo_bytes = (int64_t)(16 * hs[kStRoots] + 8 * hs[kStCand] + 8 * hs[kStListProbe] +
+                                      16 * hs[kStHashProbe] + 4 * hs[kStPairProbe]);
+        stats->tasks_split = 0;
+        stats->launches = launches;
+        stats->kernel_ms = ms;
+    }
+    if (roots_copy) cudaFreeAsync(roots_copy, s);
+    return fail(TM_OK);
+}
+
+}  // namespace tmo
