@@ -30,7 +30,7 @@ import numpy as np  # noqa: E402
 
 WORKLOADS = {
     # name: (graph spec, motifs, delta, default root sample)
-    "mid": ("MID", "CONFIG2_MOTIFS", 3600, 256),
+    "mid": ("MID", "CONFIG2_MOTIFS", 3600, 64),
     "tiny": ("TINY", "CONFIG1_MOTIFS", 10_000, 50_000),
 }
 
@@ -69,7 +69,10 @@ class ClockSampler:
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
-                 "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+                 "-lms", "100"], stdout=self.f, stderr=subprocess.DEVNULL)
+            t0 = time.time()
+            while time.time() - t0 < 5 and os.path.getsize(self.path) == 0:
+                time.sleep(0.05)
         except Exception:
             self.proc = None
         return self
@@ -178,6 +181,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-permotif", action="store_true")
+    ap.add_argument("--static", action="store_true", help="one warp per root, no subtree splitting")
     ap.add_argument("--mode", type=int, default=0, help="extra tm_count mode bits")
     args = ap.parse_args()
     if args.impl == "reference":
@@ -200,7 +204,7 @@ def main():
     counts = torch.zeros(n_m, dtype=torch.int64, device="cuda")
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
-    mode = tmotif.TM_COMINE | args.mode
+    mode = tmotif.TM_COMINE | args.mode | (0 if args.static else tmotif.TM_SCHED_DYNAMIC)
 
     def step(m):
         tmotif.tm_count(g.h, tr.h, mode=m, roots=d_roots, counts=counts, stream=stream)

@@ -22,6 +22,16 @@
 // using binary searches on the time-sorted list and the (src, dst) pair
 // index; lanes with a short window scan it instead.  Both give the count the
 // scan gives.
+//
+// Scheduling.  In the static mode each warp claims root edges from a counter
+// and mines them alone.  In the dynamic mode (TM_SCHED_DYNAMIC) the launch is
+// persistent: a warp that sees idle warps hands the unscanned half of its
+// shallowest long candidate slice to a global task queue, and idle warps take
+// tasks before new roots.  A task owns its slice exclusively (the donor
+// stops before it, and the task never moves on to the node's siblings), so
+// no match is counted twice -- the ownership rule of the paper's inter-warp
+// balancing (Section 4.5), applied to any level.  Every wait is bounded; an
+// expired wait sets an error flag that the host turns into TM_ETIMEOUT.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -38,7 +48,37 @@ constexpr int kThreads = kWarps * 32;
 constexpr int kSmemCounters = 2048;       // per-CTA counters kept in shared memory up to this many
 constexpr int kLaneScanMax = 24;          // leaf windows up to this size are scanned by the lane
 
+constexpr int kQueueCap = 1 << 20;        // tasks per launch (slots are not reused)
+constexpr int kPollEvery = 4;             // chunk loads between looks at the idle counter
+constexpr int kDonateSeq = 64;            // min unscanned entries to split a level that descends
+constexpr int kDonateLeaf = 1024;         // ... a level whose survivors are only counted
+constexpr long long kReadySpins = 1 << 22;  // bound on waiting for a claimed task's payload
+constexpr long long kIdleSpins = 1 << 20;   // bound on an idle warp's wait for work
+
 enum : int8_t { kListOut = 0, kListIn = 1, kListGlobal = 2 };
+
+// A unit of work: the slice [lo, hi) of level k's candidate list of `node`,
+// under the partial match eid[0..k-1] (eid[0] is the root edge).
+struct __align__(16) Task {
+    int32_t ri;               // root index, for per-root outputs
+    int16_t node;
+    int8_t k;
+    int8_t pad0;
+    int32_t pad1[2];
+    int32_t eid[kMaxE];
+    int64_t lo, hi;
+};
+static_assert(sizeof(Task) == 64, "task layout");
+
+struct QueueHdr {
+    unsigned long long root_cursor;
+    unsigned int head;        // next task to claim
+    unsigned int tail;        // tasks reserved by donors
+    int idle;                 // warps waiting for work
+    int busy;                 // warps holding work
+    int error;                // bit 0: a bounded wait expired
+    int pad;
+};
 
 struct Params {
     DevGraph g;
@@ -49,18 +89,21 @@ struct Params {
     unsigned long long *counts;       // n_counters
     int64_t *per_root_counts;         // [n_roots][n_counters] or null
     int64_t *per_root_work;           // [n_roots][TM_WORK_FIELDS] or null
-    unsigned long long *cursor;       // root cursor (zeroed before launch)
+    QueueHdr *q;                      // zeroed before launch
+    Task *tasks;                      // kQueueCap (dynamic mode)
+    int *ready;                       // kQueueCap publish flags, zeroed (dynamic mode)
     unsigned long long *stats;        // kStatFields totals or null
     int32_t chunk;                    // roots claimed per cursor step
     int32_t smem_counters;            // 1: per-CTA counters in shared memory
+    int32_t dynamic;                  // 1: persistent launch with task donation
 };
 
-enum { kStCand = 0, kStExp, kStListProbe, kStHashProbe, kStPairProbe, kStLeaf, kStRoots, kStatFields };
+enum { kStCand = 0, kStExp, kStListProbe, kStHashProbe, kStPairProbe, kStLeaf, kStRoots, kStSplit, kStatFields };
 
 struct WarpState {
     int2 cand[kMaxE][32];
     int64_t pos[kMaxE];       // next chunk start (absolute index into the list array)
-    int64_t end[kMaxE];       // list end
+    int64_t end[kMaxE];       // end of the candidate slice
     int64_t cbase[kMaxE];     // start of the chunk held in cand[k]
     uint32_t mask[kMaxE];     // survivors of the held chunk not yet descended
     int32_t lvert[kMaxE];     // list vertex (out/in lists)
@@ -69,6 +112,7 @@ struct WarpState {
     int16_t node[kMaxE];
     int16_t sib_end[kMaxE];
     int8_t ltype[kMaxE];
+    int8_t seq[kMaxE];        // survivors of level k are descended (not only counted)
     int32_t m2g[kMaxV];
     int32_t ehi[TM_MAX_DELTAS];
 };
@@ -181,6 +225,9 @@ __device__ int64_t pair_count(const DevGraph &g, int32_t x, int32_t w, int32_t l
     }
 }
 
+__device__ __forceinline__ int vload(const int *p) { return *(volatile const int *)p; }
+__device__ __forceinline__ unsigned int vloadu(const unsigned int *p) { return *(volatile const unsigned int *)p; }
+
 template <bool kStats>
 struct Miner {
     const Params &p;
@@ -188,10 +235,11 @@ struct Miner {
     unsigned long long *s_cnt;
     int lane;
     Work w;
-    int64_t ri;                        // root index (for per-root outputs)
+    int64_t ri;                        // root index of the current work (per-root outputs)
+    int polls;                         // chunk loads since the last look at the idle counter
 
     __device__ Miner(const Params &pp, WarpState &s, unsigned long long *c, int l)
-        : p(pp), ws(s), s_cnt(c), lane(l) {
+        : p(pp), ws(s), s_cnt(c), lane(l), polls(0) {
         for (int i = 0; i < kStatFields; i++) w.v[i] = 0;
     }
 
@@ -209,89 +257,89 @@ struct Miner {
         return l == uk ? cs : (l == vk ? cd : ws.m2g[l]);
     }
 
-    // Count the leaf edge `lv` of node L for one lane (candidate at level lv - 1
-    // with endpoints cs -> cd, edge id last), for every ref of L.
-    __device__ void leaf_eval(const DevNode &L, int lv, int uk, int vk, int32_t cs, int32_t cd, int32_t last) {
+    // Count, for one lane, the candidates of leaf edge `lv` of node L that
+    // end a match by edge id hi, after the lane's candidate (cs -> cd, id
+    // last) at level lv - 1.
+    __device__ int64_t leaf_count(const DevNode &L, int lv, int uk, int vk, int32_t cs, int32_t cd, int32_t last,
+                                  int32_t hi) {
         const DevGraph &g = p.g;
         const int u = L.eu[lv], v = L.ev[lv];
-        const int nv = L.nvb[lv];                       // mapped labels before the leaf edge
+        const int nv = L.nvb[lv];                       // labels mapped before the leaf edge
         const bool um = u < nv, vm = v < nv;
         int32_t img[kMaxV];
 #pragma unroll
         for (int l = 0; l < kMaxV; l++) img[l] = (l < nv) ? lab(l, uk, vk, cs, cd) : -1;
-        unsigned long long hp = 0, pp = 0, lp = 0;
-        for (int ri2 = 0; ri2 < L.n_ref; ri2++) {
-            const DevRef ref = p.tr.refs[L.ref_begin + ri2];
-            const int32_t hi = ws.ehi[ref.delta];
-            int64_t c = 0;
-            if (um && vm) {
-                c = pair_count(g, img[u], img[v], last, hi, hp, pp);
+        unsigned long long hp = 0, pp = 0, lp = 0, sc = 0;
+        int64_t c = 0;
+        if (um && vm) {
+            int32_t xu = u == uk ? cs : (u == vk ? cd : ws.m2g[u]);
+            int32_t xv = v == uk ? cs : (v == vk ? cd : ws.m2g[v]);
+            c = pair_count(g, xu, xv, last, hi, hp, pp);
+        } else {
+            const bool out = um;
+            const int32_t x = out ? (u == uk ? cs : (u == vk ? cd : ws.m2g[u]))
+                                  : (v == uk ? cs : (v == vk ? cd : ws.m2g[v]));
+            const int2 *adj = out ? g.out_adj : g.in_adj;
+            const int64_t *off = out ? g.out_off : g.in_off;
+            int64_t b0 = __ldg(off + x), b1 = __ldg(off + x + 1);
+            int64_t a = lane_upper(adj, b0, b1, last, lp);
+            int64_t b = lane_upper(adj, a, b1, hi, lp);
+            if (b - a <= kLaneScanMax) {
+                for (int64_t i = a; i < b; i++) {
+                    int32_t y = __ldg(&adj[i].x);
+                    bool bad = false;
+#pragma unroll
+                    for (int l = 0; l < kMaxV; l++) bad |= (l < nv) & (y == img[l]);
+                    c += !bad;
+                }
+                sc = (unsigned long long)(b - a);
             } else {
-                const bool out = um;
-                const int32_t x = out ? img[u] : img[v];
-                const int2 *adj = out ? g.out_adj : g.in_adj;
-                const int64_t *off = out ? g.out_off : g.in_off;
-                int64_t b0 = __ldg(off + x), b1 = __ldg(off + x + 1);
-                int64_t a = lane_upper(adj, b0, b1, last, lp);
-                int64_t b = lane_upper(adj, a, b1, hi, lp);
-                if (b - a <= kLaneScanMax) {
-                    for (int64_t i = a; i < b; i++) {
-                        int32_t y = __ldg(&adj[i].x);
-                        bool bad = false;
+                c = b - a;
 #pragma unroll
-                        for (int l = 0; l < kMaxV; l++) bad |= (l < nv) & (y == img[l]);
-                        c += !bad;
-                    }
-                    if (kStats) w.v[kStCand] += (unsigned long long)(b - a);
-                } else {
-                    c = b - a;
-#pragma unroll
-                    for (int l = 0; l < kMaxV; l++) {
-                        if (l < nv) c -= out ? pair_count(g, x, img[l], last, hi, hp, pp)
-                                             : pair_count(g, img[l], x, last, hi, hp, pp);
-                    }
+                for (int l = 0; l < kMaxV; l++) {
+                    if (l < nv) c -= out ? pair_count(g, x, img[l], last, hi, hp, pp)
+                                         : pair_count(g, img[l], x, last, hi, hp, pp);
                 }
             }
-            ref_total_[ri2 & 7] += (unsigned long long)c;   // accumulated per ref slot, flushed by caller
         }
         if (kStats) {
             w.v[kStHashProbe] += hp;
             w.v[kStPairProbe] += pp;
             w.v[kStListProbe] += lp;
+            w.v[kStCand] += sc;
             w.v[kStLeaf] += 1;
         }
+        return c;
     }
-    unsigned long long ref_total_[8];
 
-    // Evaluate leaf node L's last level for all survivor lanes S at level k.
+    // Leaf node L's last level for all survivor lanes S of level k, one ref at a time.
     __device__ void leaf_batch(const DevNode &L, int k, uint32_t S, int uk, int vk, int32_t cs, int32_t cd,
                                int32_t last) {
-        // refs beyond 8 are handled in groups of 8
-        for (int base = 0; base < L.n_ref; base += 8) {
-            DevNode Lg = L;
-            Lg.ref_begin = (int16_t)(L.ref_begin + base);
-            Lg.n_ref = (int16_t)min(8, L.n_ref - base);
-#pragma unroll
-            for (int i = 0; i < 8; i++) ref_total_[i] = 0;
-            if ((S >> lane) & 1u) leaf_eval(Lg, k + 1, uk, vk, cs, cd, last);
-            for (int i = 0; i < Lg.n_ref; i++) {
-                unsigned long long tot = warp_sum_u64(ref_total_[i]);
-                if (lane == 0) add_count(p.tr.refs[Lg.ref_begin + i].counter, tot);
-            }
+        for (int i = 0; i < L.n_ref; i++) {
+            const DevRef ref = p.tr.refs[L.ref_begin + i];
+            const int32_t hi = ws.ehi[ref.delta];
+            unsigned long long c = 0;
+            if (((S >> lane) & 1u) && last < hi) c = (unsigned long long)leaf_count(L, k + 1, uk, vk, cs, cd, last, hi);
+            c = warp_sum_u64(c);
+            if (lane == 0) add_count(ref.counter, c);
         }
     }
 
-    // Chunk-level work for survivors S of level k of node N; returns the
-    // mask of survivors to descend.
+    // Chunk-level work for survivors S of level k of node N: count the refs
+    // of a completed node, count single-edge leaves lane-parallel; returns
+    // the survivors to descend.
     __device__ uint32_t survivors(int k, const DevNode &N, uint32_t S, int2 c) {
         if (S == 0) return 0;
         const int uk = N.eu[k], vk = N.ev[k];
-        // endpoints of this lane's candidate
         int32_t cs, cd;
         const int8_t lt = ws.ltype[k];
         if (lt == kListOut) { cs = ws.lvert[k]; cd = c.x; }
         else if (lt == kListIn) { cs = c.x; cd = ws.lvert[k]; }
-        else { cs = ((S >> lane) & 1u) ? __ldg(p.g.src + c.y) : 0; cd = ((S >> lane) & 1u) ? __ldg(p.g.dst + c.y) : 0; }
+        else {
+            const bool mine = (S >> lane) & 1u;
+            cs = mine ? __ldg(p.g.src + c.y) : 0;
+            cd = mine ? __ldg(p.g.dst + c.y) : 0;
+        }
         const bool complete = (k == N.k_end - 1);
         if (complete && N.n_ref > 0) {                     // Q_N counted (Algorithm 3)
             for (int i = 0; i < N.n_ref; i++) {
@@ -312,19 +360,14 @@ struct Miner {
             uint32_t S2 = __ballot_sync(0xffffffffu, c.y < ws.ehi[N.dmax]) & S;
             if (S2) leaf_batch(N, k, S2, uk, vk, cs, cd, c.y);
         }
-        bool seq = complete ? (N.n_seq > 0) : !par_self;
-        return seq ? S : 0u;
+        return ws.seq[k] ? S : 0u;
     }
 
-    // Open level k for node `node` (siblings up to sib_end).
-    __device__ void open(int k, int node, int sib_end) {
-        const DevNode N = p.tr.nodes[node];
+    // Candidate list of level k of node N under the current mapping.
+    __device__ __forceinline__ void list_of(const DevNode &N, int k, int8_t &lt, int32_t &x) const {
         const int u = N.eu[k], v = N.ev[k], nv = N.nvb[k];
         const bool um = u < nv, vm = v < nv;
-        const int32_t last = ws.eid[k - 1];
-        int8_t lt;
-        int32_t x = 0;
-        int64_t b0 = 0, b1 = 0;
+        x = 0;
         if (um && vm) {
             int32_t xu = ws.m2g[u], xv = ws.m2g[v];
             int64_t du = __ldg(p.g.out_off + xu + 1) - __ldg(p.g.out_off + xu);
@@ -333,39 +376,174 @@ struct Miner {
         } else if (um) { lt = kListOut; x = ws.m2g[u]; }
         else if (vm) { lt = kListIn; x = ws.m2g[v]; }
         else { lt = kListGlobal; }
-        int64_t start;
-        if (lt == kListGlobal) {
-            b0 = (int64_t)last + 1;
-            b1 = (int64_t)ws.ehi[N.dmax] + 1;
-            start = b0;
-        } else {
-            const int64_t *off = lt == kListOut ? p.g.out_off : p.g.in_off;
-            b0 = __ldg(off + x);
-            b1 = __ldg(off + x + 1);
-            if (ws.ltype[k - 1] == lt && ws.lvert[k - 1] == x) {
-                start = ws.mpos[k - 1] + 1;             // same list as the level above
-            } else if (b1 - b0 <= 32) {
-                start = b0;                             // the chunk mask drops eids <= last
-            } else {
-                const int2 *adj = lt == kListOut ? p.g.out_adj : p.g.in_adj;
-                start = warp_upper(adj, b0, b1, last, lane, w.v[kStListProbe]);
-            }
-        }
+    }
+
+    __device__ __forceinline__ bool seq_of(const DevNode &N, int k) const {
+        const bool complete = (k == N.k_end - 1);
+        const bool par_self = (N.flags & kNodeParLeaf) && (k == N.k_end - 2);
+        return complete ? (N.n_seq > 0) : !par_self;
+    }
+
+    __device__ void set_frame(int k, int node, int sib_end, int8_t lt, int32_t x, int64_t pos, int64_t end, bool seq) {
         __syncwarp();
         if (lane == 0) {
             ws.node[k] = (int16_t)node;
             ws.sib_end[k] = (int16_t)sib_end;
             ws.ltype[k] = lt;
             ws.lvert[k] = x;
-            ws.pos[k] = start;
-            ws.end[k] = b1;
+            ws.pos[k] = pos;
+            ws.end[k] = end;
             ws.mask[k] = 0;
+            ws.seq[k] = seq ? 1 : 0;
         }
         __syncwarp();
+    }
+
+    // Open level k for node `node` (siblings up to sib_end): the slice of
+    // its list with edge ids in (eid[k-1], ehi].
+    __device__ void open(int k, int node, int sib_end) {
+        const DevNode N = p.tr.nodes[node];
+        const int32_t last = ws.eid[k - 1];
+        const int32_t hi = ws.ehi[N.dmax];
+        int8_t lt;
+        int32_t x;
+        list_of(N, k, lt, x);
+        int64_t start, end;
+        if (lt == kListGlobal) {
+            start = (int64_t)last + 1;
+            end = (int64_t)hi + 1;
+        } else {
+            const int64_t *off = lt == kListOut ? p.g.out_off : p.g.in_off;
+            const int2 *adj = lt == kListOut ? p.g.out_adj : p.g.in_adj;
+            const int64_t b0 = __ldg(off + x), b1 = __ldg(off + x + 1);
+            if (ws.ltype[k - 1] == lt && ws.lvert[k - 1] == x) start = ws.mpos[k - 1] + 1;  // same list as above
+            else if (b1 - b0 <= 32) start = b0;                 // the chunk mask drops ids <= last
+            else start = warp_upper(adj, b0, b1, last, lane, w.v[kStListProbe]);
+            end = (b1 - start <= 32) ? b1 : warp_upper(adj, start, b1, hi, lane, w.v[kStListProbe]);
+        }
+        set_frame(k, node, sib_end, lt, x, start, end, seq_of(N, k));
         if (kStats && lane == 0) w.v[kStExp]++;
     }
 
-    // Load and filter the next chunk of level k; returns survivors to descend.
+    // ---------------------------------------------------------------- tasks
+
+    // Hand [mid, end) of the shallowest long slice in levels [kbase, top] to the queue.
+    __device__ void maybe_donate(int kbase, int top) {
+        int idle = 0;
+        unsigned int tail = 0;
+        if (lane == 0) {
+            idle = vload(&p.q->idle);
+            tail = vloadu(&p.q->tail);
+        }
+        idle = __shfl_sync(0xffffffffu, idle, 0);
+        tail = __shfl_sync(0xffffffffu, tail, 0);
+        if (idle <= 0 || tail >= (unsigned int)(kQueueCap - 64)) return;
+        for (int kb = max(kbase, 1); kb <= top; kb++) {
+            const int64_t pos = ws.pos[kb], end = ws.end[kb];
+            const int64_t rem = end - pos;
+            if (rem < (ws.seq[kb] ? kDonateSeq : kDonateLeaf)) continue;
+            const int64_t mid = pos + (((rem >> 1) + 31) & ~31ll);
+            unsigned int slot = 0;
+            if (lane == 0) slot = atomicAdd(&p.q->tail, 1u);
+            slot = __shfl_sync(0xffffffffu, slot, 0);
+            if (slot >= (unsigned int)kQueueCap) return;      // full: keep the work
+            Task *tk = p.tasks + slot;
+            if (lane < kMaxE) tk->eid[lane] = lane < kb ? ws.eid[lane] : -1;
+            if (lane == 0) {
+                tk->ri = (int32_t)ri;
+                tk->node = ws.node[kb];
+                tk->k = (int8_t)kb;
+                tk->lo = mid;
+                tk->hi = end;
+                ws.end[kb] = mid;
+            }
+            __threadfence();
+            __syncwarp();
+            if (lane == 0) {
+                __threadfence();
+                atomicExch(p.ready + slot, 1);
+            }
+            if (kStats && lane == 0) w.v[kStSplit]++;
+            __syncwarp();
+            return;
+        }
+    }
+
+    // Claim a published task; false if none (or a bounded wait expired).
+    __device__ bool pop(Task &tk) {
+        int slot = -1;
+        if (lane == 0) {
+            while (true) {
+                unsigned int h = vloadu(&p.q->head);
+                unsigned int t = min(vloadu(&p.q->tail), (unsigned int)kQueueCap);
+                if (h >= t) break;
+                if (atomicCAS(&p.q->head, h, h + 1) == h) { slot = (int)h; break; }
+            }
+            if (slot >= 0) {
+                long long spins = 0;
+                while (vload(p.ready + slot) == 0) {
+                    if (++spins > kReadySpins) { atomicOr(&p.q->error, 1); slot = -2; break; }
+                    __nanosleep(64);
+                }
+                __threadfence();
+            }
+        }
+        slot = __shfl_sync(0xffffffffu, slot, 0);
+        if (slot < 0) return false;
+        __syncwarp();
+        const Task *src = p.tasks + slot;
+        tk.ri = src->ri;
+        tk.node = src->node;
+        tk.k = src->k;
+#pragma unroll
+        for (int i = 0; i < kMaxE; i++) tk.eid[i] = src->eid[i];
+        tk.lo = src->lo;
+        tk.hi = src->hi;
+        return true;
+    }
+
+    // Idle: wait (bounded) until a task is published or all work is done.
+    // Returns true when a task may be available.
+    __device__ bool wait_for_work() {
+        int r = 0;
+        if (lane == 0) {
+            atomicSub(&p.q->busy, 1);
+            atomicAdd(&p.q->idle, 1);
+            for (long long it = 0; it < kIdleSpins; it++) {
+                unsigned int h = vloadu(&p.q->head);
+                unsigned int t = min(vloadu(&p.q->tail), (unsigned int)kQueueCap);
+                if (h < t) {
+                    atomicAdd(&p.q->busy, 1);
+                    r = 1;
+                    break;
+                }
+                if (vload(&p.q->busy) == 0) {
+                    __threadfence();
+                    h = vloadu(&p.q->head);
+                    t = min(vloadu(&p.q->tail), (unsigned int)kQueueCap);
+                    if (h >= t) break;                   // nothing queued, nobody working: done
+                }
+                __nanosleep(256);
+            }
+            atomicSub(&p.q->idle, 1);
+        }
+        return __shfl_sync(0xffffffffu, r, 0) != 0;
+    }
+
+    // ---------------------------------------------------------------- mining
+
+    // Windows of every distinct delta for root r.
+    __device__ void windows(int32_t r) {
+        const int64_t tr0 = __ldg(p.g.t + r);
+        for (int j = lane; j < p.tr.n_deltas; j += 32) {
+            unsigned long long pr = 0;
+            ws.ehi[j] = window_end(p.g.t, p.g.E, r, sat_add(tr0, __ldg(p.tr.deltas + j)), pr);
+            if (kStats) w.v[kStListProbe] += pr;
+        }
+        __syncwarp();
+    }
+
+    // Load and filter the next chunk of level k.
     __device__ void load_chunk(int k) {
         const DevNode N = p.tr.nodes[ws.node[k]];
         const int8_t lt = ws.ltype[k];
@@ -406,47 +584,22 @@ struct Miner {
         const uint32_t VB = __ballot_sync(0xffffffffu, valid);
         if (kStats && lane == 0) w.v[kStCand] += (unsigned long long)__popc(VB);
         ws.cand[k][lane] = c;
-        uint32_t D = survivors(k, N, S, c);
         __syncwarp();
         if (lane == 0) {
             ws.cbase[k] = base;
             ws.pos[k] = outw ? end : base + 32;
-            ws.mask[k] = D;
         }
+        uint32_t D = survivors(k, N, S, c);
+        __syncwarp();
+        if (lane == 0) ws.mask[k] = D;
         __syncwarp();
     }
 
-    __device__ void root(int32_t r) {
+    // Depth-first walk of the frames from level `kbase` up.
+    __device__ void run(int kbase) {
         const DevGraph &g = p.g;
-        const int32_t a = __ldg(g.src + r), b = __ldg(g.dst + r);
-        if (a == b) return;                             // injective map needs a != b
-        const int64_t tr0 = __ldg(g.t + r);
-        for (int j = lane; j < p.tr.n_deltas; j += 32) {
-            unsigned long long pr = 0;
-            ws.ehi[j] = window_end(g.t, g.E, r, sat_add(tr0, __ldg(p.tr.deltas + j)), pr);
-            if (kStats) w.v[kStListProbe] += pr;
-        }
-        if (lane == 0) {
-            ws.ltype[0] = kListGlobal;
-            ws.lvert[0] = -1;
-            ws.node[0] = 0;
-            ws.sib_end[0] = 1;
-            ws.pos[0] = 0;
-            ws.end[0] = 0;
-            ws.cbase[0] = r;
-        }
-        __syncwarp();
-        // level 0: the root edge as a one-candidate chunk on lane 0
-        const DevNode N0 = p.tr.nodes[0];
-        int2 c = make_int2(lane == 0 ? b : 0, lane == 0 ? r : 0);
-        ws.cand[0][lane] = c;
-        uint32_t D = survivors(0, N0, 1u, c);
-        __syncwarp();
-        if (lane == 0) ws.mask[0] = D;
-        __syncwarp();
-
-        int k = 0;
-        while (k >= 0) {
+        int k = kbase;
+        while (k >= kbase) {
             uint32_t m = ws.mask[k];
             if (m) {
                 const int j = __ffs(m) - 1;
@@ -478,6 +631,10 @@ struct Miner {
                 continue;
             }
             if (ws.pos[k] < ws.end[k]) {
+                if (p.dynamic && ++polls >= kPollEvery) {
+                    polls = 0;
+                    maybe_donate(kbase, k);
+                }
                 load_chunk(k);
                 continue;
             }
@@ -488,7 +645,63 @@ struct Miner {
             k--;
         }
     }
+
+    // Root edge r as the first motif edge (Algorithm 1, first call).
+    __device__ void root(int32_t r) {
+        const DevGraph &g = p.g;
+        const int32_t a = __ldg(g.src + r), b = __ldg(g.dst + r);
+        if (a == b) return;                             // injective map needs a != b
+        windows(r);
+        const DevNode N0 = p.tr.nodes[0];
+        set_frame(0, 0, 1, kListGlobal, -1, 0, 0, seq_of(N0, 0));
+        if (lane == 0) ws.cbase[0] = r;
+        // level 0: the root edge as a one-candidate chunk on lane 0
+        int2 c = make_int2(lane == 0 ? b : 0, lane == 0 ? r : 0);
+        ws.cand[0][lane] = c;
+        __syncwarp();
+        uint32_t D = survivors(0, N0, 1u, c);
+        __syncwarp();
+        if (lane == 0) ws.mask[0] = D;
+        __syncwarp();
+        run(0);
+    }
+
+    // A donated slice: rebuild the partial match, then walk its subtree.
+    __device__ void task(const Task &tk) {
+        const DevGraph &g = p.g;
+        const int k = tk.k;
+        windows(tk.eid[0]);
+        const DevNode N = p.tr.nodes[tk.node];
+        if (lane == 0) {
+            for (int i = 0; i < k; i++) {
+                const int32_t e = tk.eid[i];
+                ws.eid[i] = e;
+                ws.m2g[N.eu[i]] = __ldg(g.src + e);
+                ws.m2g[N.ev[i]] = __ldg(g.dst + e);
+            }
+        }
+        __syncwarp();
+        int8_t lt;
+        int32_t x;
+        list_of(N, k, lt, x);
+        set_frame(k, tk.node, tk.node + 1, lt, x, tk.lo, tk.hi, seq_of(N, k));
+        run(k);
+    }
 };
+
+template <bool kStats>
+__device__ void flush_work(Miner<kStats> &M, const Work &before, const Params &p, int lane) {
+    if (!kStats || !p.per_root_work) return;
+    unsigned long long d[4];
+    d[0] = warp_sum_u64(M.w.v[kStCand] - before.v[kStCand]);
+    d[1] = warp_sum_u64(M.w.v[kStExp] - before.v[kStExp]);
+    d[2] = warp_sum_u64(M.w.v[kStListProbe] + M.w.v[kStHashProbe] + M.w.v[kStPairProbe] -
+                        before.v[kStListProbe] - before.v[kStHashProbe] - before.v[kStPairProbe]);
+    d[3] = warp_sum_u64(M.w.v[kStLeaf] - before.v[kStLeaf]);
+    if (lane == 0)
+        for (int f = 0; f < 4; f++)
+            if (d[f]) atomicAdd((unsigned long long *)&p.per_root_work[M.ri * TM_WORK_FIELDS + f], d[f]);
+}
 
 template <bool kStats>
 __global__ void __launch_bounds__(kThreads) k_mine(Params p) {
@@ -499,32 +712,34 @@ __global__ void __launch_bounds__(kThreads) k_mine(Params p) {
         for (int i = threadIdx.x; i < p.tr.n_counters; i += blockDim.x) s_cnt[i] = 0;
     __syncthreads();
     Miner<kStats> M(p, s_ws[warp], s_cnt, lane);
+    if (p.dynamic && lane == 0) atomicAdd(&p.q->busy, 1);
     while (true) {
-        unsigned long long first = 0;
-        if (lane == 0) first = atomicAdd(p.cursor, (unsigned long long)p.chunk);
-        first = __shfl_sync(0xffffffffu, first, 0);
-        if (first >= (unsigned long long)p.n_roots) break;
-        const int64_t last = min((int64_t)first + p.chunk, p.n_roots);
-        for (int64_t ri = (int64_t)first; ri < last; ri++) {
-            M.ri = ri;
-            const int32_t r = p.roots ? __ldg(p.roots + ri) : (int32_t)(p.root_lo + ri);
-            Work before = M.w;
-            M.root(r);
-            if (kStats) {
-                if (lane == 0) M.w.v[kStRoots]++;
-                if (p.per_root_work) {
-                    // lane partials are summed; each lane holds its own probe counts
-                    unsigned long long d[4];
-                    d[0] = warp_sum_u64(M.w.v[kStCand] - before.v[kStCand]);
-                    d[1] = warp_sum_u64(M.w.v[kStExp] - before.v[kStExp]);
-                    d[2] = warp_sum_u64(M.w.v[kStListProbe] + M.w.v[kStHashProbe] + M.w.v[kStPairProbe] -
-                                        before.v[kStListProbe] - before.v[kStHashProbe] - before.v[kStPairProbe]);
-                    d[3] = warp_sum_u64(M.w.v[kStLeaf] - before.v[kStLeaf]);
-                    if (lane == 0)
-                        for (int f = 0; f < 4; f++) p.per_root_work[ri * TM_WORK_FIELDS + f] = (int64_t)d[f];
-                }
+        if (p.dynamic) {
+            Task tk;
+            if (M.pop(tk)) {
+                M.ri = tk.ri;
+                Work before = M.w;
+                M.task(tk);
+                flush_work(M, before, p, lane);
+                continue;
             }
         }
+        unsigned long long first = 0;
+        if (lane == 0) first = atomicAdd(&p.q->root_cursor, (unsigned long long)p.chunk);
+        first = __shfl_sync(0xffffffffu, first, 0);
+        if (first < (unsigned long long)p.n_roots) {
+            const int64_t last = min((int64_t)first + p.chunk, p.n_roots);
+            for (int64_t ri = (int64_t)first; ri < last; ri++) {
+                M.ri = ri;
+                const int32_t r = p.roots ? __ldg(p.roots + ri) : (int32_t)(p.root_lo + ri);
+                Work before = M.w;
+                M.root(r);
+                if (kStats && lane == 0) M.w.v[kStRoots]++;
+                flush_work(M, before, p, lane);
+            }
+            continue;
+        }
+        if (!p.dynamic || !M.wait_for_work()) break;
     }
     if (kStats) {
         for (int f = 0; f < kStatFields; f++) {
@@ -543,11 +758,6 @@ __global__ void k_to_i64(const unsigned long long *a, int64_t *b, int n) {
     if (i < n) b[i] = (int64_t)a[i];
 }
 
-struct LaunchShape {
-    int blocks;
-    int smem;
-};
-
 }  // namespace
 
 int mine(const tm_graph *g, const tm_tree *tr, const tm_count_args *args, int64_t *counts,
@@ -555,6 +765,7 @@ int mine(const tm_graph *g, const tm_tree *tr, const tm_count_args *args, int64_
     const int n_motifs = tr->h.n_motifs;
     const bool comine = (args->mode & TM_PERMOTIF) == 0;
     const bool par = (args->mode & TM_LEAF_SCAN) == 0;
+    const bool dynamic = (args->mode & TM_SCHED_DYNAMIC) != 0;
     const bool want_stats = stats != nullptr;
     int64_t n_roots;
     if (args->roots) {
@@ -568,39 +779,48 @@ int mine(const tm_graph *g, const tm_tree *tr, const tm_count_args *args, int64_
         n_roots = hi - args->root_lo;
     }
     if (n_roots < 0) { set_error("tm_count: n_roots < 0"); return TM_EINVAL; }
-
-    // device scratch: counters, root cursors (one per launch), stats
-    const int n_launch = comine ? 1 : (int)tr->chains.size();
-    size_t bytes = sizeof(unsigned long long) * ((size_t)n_motifs + (size_t)n_launch + kStatFields);
-    void *scratch = nullptr;
-    TM_CUDA_TRY(cudaMallocAsync(&scratch, bytes, s));
-    unsigned long long *d_cnt = (unsigned long long *)scratch;
-    unsigned long long *d_cur = d_cnt + n_motifs;
-    unsigned long long *d_st = d_cur + n_launch;
-    int rc = TM_OK;
-    cudaEvent_t e0 = nullptr, e1 = nullptr;
-    auto fail = [&](int code) {
-        if (e0) cudaEventDestroy(e0);
-        if (e1) cudaEventDestroy(e1);
-        cudaFreeAsync(scratch, s);
-        return code;
-    };
-    if (cudaMemsetAsync(scratch, 0, bytes, s) != cudaSuccess) { set_error("tm_count: memset"); return fail(TM_ECUDA); }
-
-    // validate a host root list up front; device lists are checked by the caller's contract
     if (args->roots && !(args->flags & TM_ROOTS_DEVICE)) {
         for (int64_t i = 0; i < n_roots; i++)
             if (args->roots[i] < 0 || args->roots[i] >= g->d.E) {
                 set_error("tm_count: root edge id out of range");
-                return fail(TM_EINVAL);
+                return TM_EINVAL;
             }
     }
-    const int32_t *d_roots = args->roots;
+
+    // device scratch: counters, stats, one queue header per launch, task queue
+    const int n_launch = comine ? 1 : (int)tr->chains.size();
+    const size_t b_cnt = sizeof(unsigned long long) * (size_t)(n_motifs + kStatFields);
+    const size_t o_q = (b_cnt + 255) / 256 * 256;
+    const size_t b_q = sizeof(QueueHdr) * (size_t)n_launch;
+    const size_t o_tasks = (o_q + b_q + 255) / 256 * 256;
+    const size_t b_tasks = dynamic ? sizeof(Task) * kQueueCap : 0;
+    const size_t o_ready = o_tasks + b_tasks;
+    const size_t b_ready = dynamic ? sizeof(int) * kQueueCap : 0;
+    const size_t bytes = o_ready + b_ready;
+    char *scratch = nullptr;
+    TM_CUDA_TRY(cudaMallocAsync((void **)&scratch, bytes, s));
+    unsigned long long *d_cnt = (unsigned long long *)scratch;
+    unsigned long long *d_st = d_cnt + n_motifs;
+    QueueHdr *d_q = (QueueHdr *)(scratch + o_q);
+    Task *d_tasks = dynamic ? (Task *)(scratch + o_tasks) : nullptr;
+    int *d_ready = dynamic ? (int *)(scratch + o_ready) : nullptr;
     void *roots_copy = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    auto finish = [&](int code) {
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+        if (roots_copy) cudaFreeAsync(roots_copy, s);
+        cudaFreeAsync(scratch, s);
+        return code;
+    };
+    // ready flags only need zeroing between launches; counters and headers once
+    if (cudaMemsetAsync(scratch, 0, o_tasks, s) != cudaSuccess) { set_error("tm_count: memset"); return finish(TM_ECUDA); }
+
+    const int32_t *d_roots = args->roots;
     if (args->roots && !(args->flags & TM_ROOTS_DEVICE) && n_roots > 0) {
         if (cudaMallocAsync(&roots_copy, sizeof(int32_t) * n_roots, s) != cudaSuccess) {
             set_error("tm_count: root list allocation");
-            return fail(TM_ENOMEM);
+            return finish(TM_ENOMEM);
         }
         cudaMemcpyAsync(roots_copy, args->roots, sizeof(int32_t) * n_roots, cudaMemcpyHostToDevice, s);
         d_roots = (const int32_t *)roots_copy;
@@ -632,8 +852,9 @@ int mine(const tm_graph *g, const tm_tree *tr, const tm_count_args *args, int64_
     int64_t launches = 0;
     for (int L = 0; L < n_launch && n_roots > 0; L++) {
         DevTree dt;
-        rc = tree_device(tr, comine ? 0 : 1 + L, par, s, &dt);
-        if (rc != TM_OK) return fail(rc);
+        int rc = tree_device(tr, comine ? 0 : 1 + L, par, s, &dt);
+        if (rc != TM_OK) return finish(rc);
+        if (dynamic && L > 0) cudaMemsetAsync(d_ready, 0, b_ready, s);
         Params prm;
         prm.g = g->d;
         prm.tr = dt;
@@ -642,21 +863,40 @@ int mine(const tm_graph *g, const tm_tree *tr, const tm_count_args *args, int64_
         prm.root_lo = args->roots ? 0 : args->root_lo;
         prm.counts = d_cnt;
         prm.per_root_counts = args->per_root_counts;
-        prm.per_root_work = (L == 0) ? args->per_root_work : nullptr;
-        prm.cursor = d_cur + L;
+        prm.per_root_work = args->per_root_work;
+        prm.q = d_q + L;
+        prm.tasks = d_tasks;
+        prm.ready = d_ready;
         prm.stats = d_st;
         prm.chunk = chunk;
         prm.smem_counters = smem_cnt ? 1 : 0;
+        prm.dynamic = dynamic ? 1 : 0;
+        if (dynamic && L == 0) cudaMemsetAsync(d_ready, 0, b_ready, s);
         kern<<<blocks, kThreads, dyn_smem, s>>>(prm);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) {
             set_error(std::string("tm_count: launch: ") + cudaGetErrorString(e));
-            return fail(TM_ECUDA);
+            return finish(TM_ECUDA);
         }
         launches++;
     }
     if (want_stats) cudaEventRecord(e1, s);
 
+    // the dynamic mode reports expired waits; that needs the queue headers back
+    if (dynamic) {
+        std::vector<QueueHdr> hq(n_launch);
+        cudaMemcpyAsync(hq.data(), d_q, sizeof(QueueHdr) * n_launch, cudaMemcpyDeviceToHost, s);
+        cudaError_t e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) {
+            set_error(std::string("tm_count: ") + cudaGetErrorString(e));
+            return finish(TM_ECUDA);
+        }
+        for (auto &q : hq)
+            if (q.error) {
+                set_error("tm_count: a bounded device wait expired; counts are incomplete");
+                return finish(TM_ETIMEOUT);
+            }
+    }
     if (args->flags & TM_COUNTS_DEVICE) {
         k_to_i64<<<(n_motifs + 255) / 256, 256, 0, s>>>(d_cnt, counts, n_motifs);
     } else {
@@ -665,7 +905,7 @@ int mine(const tm_graph *g, const tm_tree *tr, const tm_count_args *args, int64_
         cudaError_t e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) {
             set_error(std::string("tm_count: ") + cudaGetErrorString(e));
-            return fail(TM_ECUDA);
+            return finish(TM_ECUDA);
         }
         for (int i = 0; i < n_motifs; i++) counts[i] = (int64_t)h[i];
     }
@@ -675,7 +915,7 @@ int mine(const tm_graph *g, const tm_tree *tr, const tm_count_args *args, int64_
         cudaError_t e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) {
             set_error(std::string("tm_count: ") + cudaGetErrorString(e));
-            return fail(TM_ECUDA);
+            return finish(TM_ECUDA);
         }
         float ms = 0;
         cudaEventElapsedTime(&ms, e0, e1);
@@ -687,12 +927,11 @@ int mine(const tm_graph *g, const tm_tree *tr, const tm_count_args *args, int64_
         stats->leaf_evals = (int64_t)hs[kStLeaf];
         stats->algo_bytes = (int64_t)(16 * hs[kStRoots] + 8 * hs[kStCand] + 8 * hs[kStListProbe] +
                                       16 * hs[kStHashProbe] + 4 * hs[kStPairProbe]);
-        stats->tasks_split = 0;
+        stats->tasks_split = (int64_t)hs[kStSplit];
         stats->launches = launches;
         stats->kernel_ms = ms;
     }
-    if (roots_copy) cudaFreeAsync(roots_copy, s);
-    return fail(TM_OK);
+    return finish(TM_OK);
 }
 
 }  // namespace tmo
