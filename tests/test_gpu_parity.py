@@ -86,9 +86,9 @@ def test_pin_motifs_small_graphs(seed, name, mode):
 
 @pytest.mark.parametrize("seed", range(6))
 def test_random_trees_multi_delta(seed):
-    src, dst, t = synth.tiny_graph(9100 + seed, 40, 6000, 30000, zipf_s=1.3)
+    src, dst, t = synth.tiny_graph(9100 + seed, 40, 3000, 60000, zipf_s=1.3)
     motifs = synth.random_motif_tree(500 + seed, max_edges=5, max_motifs=20)
-    deltas = [[600, 2000, 5000][(i + seed) % 3] for i in range(len(motifs))]
+    deltas = [[300, 1000, 2000][(i + seed) % 3] for i in range(len(motifs))]
     g = tmotif.Graph(src, dst, t, 40, presorted=True)
     tr = tmotif.Tree(motifs, deltas)
     want = [oracle.count_motif(src, dst, t, m, d, n_nodes=40) for m, d in zip(motifs, deltas)]
@@ -98,14 +98,14 @@ def test_random_trees_multi_delta(seed):
 
 def test_max_size_motifs():
     # 8 edges and 8 vertices: a 7-edge path closed back, and an 8-cycle
-    src, dst, t = synth.tiny_graph(9200, 8, 3000, 4000, zipf_s=0.3)
+    src, dst, t = synth.tiny_graph(9200, 8, 1500, 4000, zipf_s=0.3)
     cyc8 = tuple((i, (i + 1) % 8) for i in range(8))
     path7 = tuple((i, i + 1) for i in range(7))
     star = tuple((0, i + 1) for i in range(7)) + ((1, 0),)
     motifs = [cyc8, path7, star]
     g = tmotif.Graph(src, dst, t, 8, presorted=True)
-    tr = tmotif.Tree(motifs, 400)
-    want = [oracle.count_motif(src, dst, t, m, 400, n_nodes=8) for m in motifs]
+    tr = tmotif.Tree(motifs, 150)
+    want = [oracle.count_motif(src, dst, t, m, 150, n_nodes=8) for m in motifs]
     for _, mode in MODES:
         assert tmotif.count(g, tr, mode=mode).tolist() == want
 
@@ -229,7 +229,7 @@ def test_mid_config_comine_modes_agree(mid):
     candidates per root and motif): co-mined and per-motif, scan and window
     arithmetic, and the oracle all agree exactly."""
     src, dst, t, g = mid
-    roots = synth.root_sample(22, len(src), 48)
+    roots = synth.root_sample(22, len(src), 64)
     ms = [synth.CONFIG2_MOTIFS[i] for i in (0, 1, 3, 4, 6, 7, 9, 10)]
     keep = np.ones(len(roots), bool)
     cols = []
@@ -238,7 +238,7 @@ def test_mid_config_comine_modes_agree(mid):
                                    root_budget=2_000_000)
         cols.append(pr)
         keep &= pr >= 0
-    assert keep.sum() >= 8
+    assert keep.sum() >= 5
     want = np.stack(cols, axis=1)[keep].sum(axis=0)
     tr = tmotif.Tree(ms, synth.MID_DELTA)
     sub = roots[keep]
