@@ -192,6 +192,39 @@ typedef struct {
 int tm_count(const tm_graph *g, const tm_tree *tr, const tm_count_args *args, int64_t *counts,
              tm_run_stats *stats, void *stream);
 
+/*
+ * Allocation-free counting.  The paper has no counterpart: this is a
+ * service of the library.
+ *
+ * Some callers must not allocate device memory while they count: a
+ * long-running service that fixed its memory budget at start-up, code under
+ * an external allocator that rejects stray cudaMalloc calls, or a loop with
+ * a latency limit that an allocation could break.  tm_count allocates its
+ * scratch (counters, root cursor, task queue) on every call; this variant
+ * allocates nothing.  Its scratch is one static device array of 256 KiB in
+ * the library, which every GPU that loads the library holds until the
+ * process exits.
+ *
+ * It counts like tm_count with mode TM_COMINE (MG-Tree, window-arithmetic
+ * leaves) and static scheduling (one warp per root edge), same counts.
+ *   roots:  device array of n_roots root edge ids, or NULL for the eids
+ *           [root_lo, root_hi) (root_hi <= 0 means n_edges)
+ *   counts: device array of n_motifs int64, overwritten; the call does not
+ *           synchronise `stream`
+ * Limits: at most 1024 motifs and a tree node table of at most 240 KiB
+ * (about 3000 nodes); beyond them the call returns TM_EUNSUPPORTED.
+ * Set-up: the first call on a device (made with that device current)
+ * looks up the address of the static array there; make that first call
+ * before any stream capture.  All calls share the one array, which keeps the
+ * last call's contents; each call clears its counters itself, but calls
+ * whose work overlaps on the GPU (several streams or threads at once) race
+ * on the array and give wrong counts, so serialise them.
+ * Errors: TM_EINVAL (NULL handle or counts, bad root range, n_roots < 0),
+ * TM_EUNSUPPORTED (limits above), TM_ECUDA.
+ */
+int tm_count_noalloc(const tm_graph *g, const tm_tree *tr, const int32_t *roots, int64_t n_roots,
+                     int64_t root_lo, int64_t root_hi, int64_t *counts, void *stream);
+
 /* Message describing the last error on the calling thread ("" if none). */
 const char *tm_last_error(void);
 

@@ -132,6 +132,16 @@ struct HostTree {
 }  // namespace tmo
 
 namespace tmo {
+// The device node table of a tree as one host byte image: nodes, then refs
+// at o_refs, then the window table at o_deltas (offsets 256-byte aligned).
+struct TreeImage {
+    std::vector<char> bytes;
+    size_t o_refs = 0, o_deltas = 0;
+    int32_t n_nodes = 0, n_refs = 0, n_deltas = 0, n_counters = 0;
+};
+DevTree image_tree(const TreeImage &img, const void *dev);
+void tree_image(const HostTree &h, bool par_leaves, TreeImage *img);
+
 // A tree uploaded to the device once, on first use, per leaf mode.
 struct DevTreeCache {
     bool ready = false;
@@ -146,6 +156,7 @@ struct tm_tree {
     // device copies: [leaf mode][0 = MG-Tree, 1 + i = chain i]
     std::vector<tmo::DevTreeCache> dev[2];
     void *mutex = nullptr;               // std::mutex guarding the lazy upload
+    tmo::TreeImage image;                // MG-Tree node table (window-arithmetic leaves), built once
 };
 
 namespace tmo {

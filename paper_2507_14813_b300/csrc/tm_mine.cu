@@ -935,3 +935,116 @@ int mine(const tm_graph *g, const tm_tree *tr, const tm_count_args *args, int64_
 }
 
 }  // namespace tmo
+
+// ---------------------------------------------------------------------------
+// Allocation-free counting.
+//
+// For callers that may not allocate device memory while they count: code
+// that runs between the set-up and tear-down of a long-lived service with a
+// fixed memory budget, under an external allocator that forbids stray
+// cudaMalloc calls, or with a latency limit that an allocation could break.
+// The graph and tree handles are built beforehand (that does allocate); the
+// counting call below then uses only the static array that follows, which
+// every GPU that loads this library holds until the process exits.
+#include <mutex>
+
+namespace tmo {
+namespace {
+
+constexpr size_t kNoAllocBytes = 256u << 10;          // 256 KiB in total
+constexpr int kNoAllocMaxMotifs = 1024;               // counters: 8 KiB
+constexpr size_t kNoAllocHdr = 8u << 10;              // queue header at 8 KiB
+constexpr size_t kNoAllocTree = 16u << 10;            // tree image from 16 KiB to the end
+constexpr size_t kNoAllocMaxTree = kNoAllocBytes - kNoAllocTree;
+constexpr int kNoAllocMaxDevices = 64;
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+std::mutex g_noalloc_mu;
+void *g_noalloc_ptr[kNoAllocMaxDevices];
+
+// Device address of the static array on the current device (looked up once per device).
+int noalloc_scratch(int dev, void **out) {
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void *ptr = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+        if (e != cudaSuccess) {
+            set_error(std::string("tm_count_noalloc: cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+            return TM_ECUDA;
+        }
+        g_noalloc_ptr[dev] = ptr;
+    }
+    *out = g_noalloc_ptr[dev];
+    return TM_OK;
+}
+
+}  // namespace
+}  // namespace tmo
+
+extern "C" int tm_count_noalloc(const tm_graph *g, const tm_tree *tr, const int32_t *roots, int64_t n_roots,
+                                int64_t root_lo, int64_t root_hi, int64_t *counts, void *stream) {
+    using namespace tmo;
+    if (!g || !tr || !counts) { set_error("tm_count_noalloc: NULL argument"); return TM_EINVAL; }
+    const int n_motifs = tr->h.n_motifs;
+    if (n_motifs > kNoAllocMaxMotifs) {
+        set_error("tm_count_noalloc: more than 1024 motifs do not fit its static scratch");
+        return TM_EUNSUPPORTED;
+    }
+    const TreeImage &img = tr->image;
+    if (img.bytes.size() > kNoAllocMaxTree) {
+        set_error("tm_count_noalloc: tree node table larger than 240 KiB does not fit its static scratch");
+        return TM_EUNSUPPORTED;
+    }
+    if (roots) {
+        if (n_roots < 0) { set_error("tm_count_noalloc: n_roots < 0"); return TM_EINVAL; }
+    } else {
+        int64_t hi = root_hi > 0 ? root_hi : g->d.E;
+        if (root_lo < 0 || hi > g->d.E || root_lo > hi) {
+            set_error("tm_count_noalloc: root range outside [0, n_edges]");
+            return TM_EINVAL;
+        }
+        n_roots = hi - root_lo;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    int dev = 0;
+    TM_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kNoAllocMaxDevices) { set_error("tm_count_noalloc: device index too large"); return TM_EUNSUPPORTED; }
+    void *base = nullptr;
+    TM_TRY(noalloc_scratch(dev, &base));
+    char *b = (char *)base;
+    unsigned long long *d_cnt = (unsigned long long *)b;
+    QueueHdr *d_q = (QueueHdr *)(b + kNoAllocHdr);
+    // counters and the root cursor start at zero on every call
+    TM_CUDA_TRY(cudaMemsetAsync(b, 0, kNoAllocTree, s));
+    TM_CUDA_TRY(cudaMemcpyAsync(b + kNoAllocTree, img.bytes.data(), img.bytes.size(), cudaMemcpyHostToDevice, s));
+    if (n_roots > 0) {
+        int n_sm = 0, per_sm = 0;
+        TM_CUDA_TRY(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev));
+        const int dyn_smem = (int)(sizeof(unsigned long long) * n_motifs);
+        TM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_mine<false>, kThreads, dyn_smem));
+        per_sm = std::max(per_sm, 1);
+        const int blocks = n_sm * per_sm;
+        Params prm;
+        prm.g = g->d;
+        prm.tr = image_tree(img, b + kNoAllocTree);
+        prm.roots = roots;
+        prm.n_roots = n_roots;
+        prm.root_lo = roots ? 0 : root_lo;
+        prm.counts = d_cnt;
+        prm.per_root_counts = nullptr;
+        prm.per_root_work = nullptr;
+        prm.q = d_q;
+        prm.tasks = nullptr;
+        prm.ready = nullptr;
+        prm.stats = nullptr;
+        prm.chunk = (int32_t)std::max<int64_t>(1, std::min<int64_t>(16, n_roots / ((int64_t)blocks * kWarps * 64)));
+        prm.smem_counters = 1;
+        prm.dynamic = 0;
+        k_mine<false><<<blocks, kThreads, dyn_smem, s>>>(prm);
+        TM_CUDA_TRY(cudaGetLastError());
+    }
+    k_to_i64<<<(n_motifs + 255) / 256, 256, 0, s>>>(d_cnt, counts, n_motifs);
+    TM_CUDA_TRY(cudaGetLastError());
+    return TM_OK;
+}

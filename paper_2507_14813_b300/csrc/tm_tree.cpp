@@ -192,6 +192,7 @@ int tree_build(const int8_t *uv, const int32_t *off, int32_t n, const int64_t *d
     tr->dev[0].resize(1 + tr->chains.size());
     tr->dev[1].resize(1 + tr->chains.size());
     tr->mutex = new std::mutex();
+    tree_image(h, true, &tr->image);
     *out = tr.release();
     return TM_OK;
 }
@@ -202,7 +203,7 @@ namespace {
 // breadth-first so that each node's children are contiguous; among them the
 // children descended one candidate at a time come first and the single-edge
 // leaves counted in parallel last.
-int upload(const HostTree &h, bool par_leaves, DevTree *d, void **mem) {
+void flatten(const HostTree &h, bool par_leaves, TreeImage *img) {
     const int nn = (int)h.nodes.size();
     // distinct windows and per-motif delta index
     std::vector<int64_t> ds;
@@ -286,33 +287,51 @@ int upload(const HostTree &h, bool par_leaves, DevTree *d, void **mem) {
     size_t b_nodes = sizeof(DevNode) * nodes.size();
     size_t b_refs = sizeof(DevRef) * std::max<size_t>(refs.size(), 1);
     size_t b_ds = sizeof(int64_t) * std::max<size_t>(ds.size(), 1);
-    size_t o_refs = (b_nodes + 255) / 256 * 256;
-    size_t o_ds = o_refs + (b_refs + 255) / 256 * 256;
-    size_t total = o_ds + b_ds;
-    std::vector<char> host(total, 0);
-    memcpy(host.data(), nodes.data(), b_nodes);
-    if (!refs.empty()) memcpy(host.data() + o_refs, refs.data(), sizeof(DevRef) * refs.size());
-    if (!ds.empty()) memcpy(host.data() + o_ds, ds.data(), sizeof(int64_t) * ds.size());
+    img->o_refs = (b_nodes + 255) / 256 * 256;
+    img->o_deltas = img->o_refs + (b_refs + 255) / 256 * 256;
+    img->bytes.assign(img->o_deltas + b_ds, 0);
+    memcpy(img->bytes.data(), nodes.data(), b_nodes);
+    if (!refs.empty()) memcpy(img->bytes.data() + img->o_refs, refs.data(), sizeof(DevRef) * refs.size());
+    if (!ds.empty()) memcpy(img->bytes.data() + img->o_deltas, ds.data(), sizeof(int64_t) * ds.size());
+    img->n_nodes = nn;
+    img->n_refs = (int32_t)refs.size();
+    img->n_deltas = (int32_t)ds.size();
+    img->n_counters = h.n_motifs;
+}
+
+int upload(const HostTree &h, bool par_leaves, DevTree *d, void **mem) {
+    TreeImage img;
+    flatten(h, par_leaves, &img);
+    const size_t total = img.bytes.size();
     char *dev = nullptr;
     TM_CUDA_TRY(cudaMalloc(&dev, total));
-    cudaError_t e = cudaMemcpy(dev, host.data(), total, cudaMemcpyHostToDevice);
+    cudaError_t e = cudaMemcpy(dev, img.bytes.data(), total, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
         cudaFree(dev);
         set_error(std::string("tree upload: ") + cudaGetErrorString(e));
         return TM_ECUDA;
     }
-    d->nodes = (const DevNode *)dev;
-    d->refs = (const DevRef *)(dev + o_refs);
-    d->deltas = (const int64_t *)(dev + o_ds);
-    d->n_nodes = nn;
-    d->n_refs = (int32_t)refs.size();
-    d->n_deltas = (int32_t)ds.size();
-    d->n_counters = h.n_motifs;
+    *d = image_tree(img, dev);
     *mem = dev;
     return TM_OK;
 }
 
 }  // namespace
+
+void tree_image(const HostTree &h, bool par_leaves, TreeImage *img) { flatten(h, par_leaves, img); }
+
+DevTree image_tree(const TreeImage &img, const void *dev) {
+    DevTree d;
+    const char *b = (const char *)dev;
+    d.nodes = (const DevNode *)b;
+    d.refs = (const DevRef *)(b + img.o_refs);
+    d.deltas = (const int64_t *)(b + img.o_deltas);
+    d.n_nodes = img.n_nodes;
+    d.n_refs = img.n_refs;
+    d.n_deltas = img.n_deltas;
+    d.n_counters = img.n_counters;
+    return d;
+}
 
 int tree_device(const tm_tree *trc, int which, bool par_leaves, cudaStream_t s, DevTree *out) {
     (void)s;

@@ -87,8 +87,8 @@ class tm_run_stats(ctypes.Structure):
 _lib = None
 
 EXPORTS = ("tm_graph_load", "tm_graph_get_info", "tm_graph_edges", "tm_graph_free", "tm_tree_build",
-           "tm_tree_get_info", "tm_tree_get_node", "tm_tree_free", "tm_count", "tm_last_error",
-           "tm_version")
+           "tm_tree_get_info", "tm_tree_get_node", "tm_tree_free", "tm_count", "tm_count_noalloc",
+           "tm_last_error", "tm_version")
 
 
 def lib():
@@ -108,6 +108,7 @@ def lib():
         L.tm_tree_get_node.argtypes = [P, i32, ctypes.POINTER(tm_tree_node)]
         L.tm_tree_free.argtypes = [P]
         L.tm_count.argtypes = [P, P, ctypes.POINTER(tm_count_args), P, ctypes.POINTER(tm_run_stats), P]
+        L.tm_count_noalloc.argtypes = [P, P, P, i64, i64, i64, P, P]
         L.tm_last_error.restype = ctypes.c_char_p
         L.tm_version.restype = ctypes.c_char_p
         for name in EXPORTS:
@@ -265,6 +266,26 @@ def tm_count(g, tr, mode: int = TM_COMINE, roots=None, root_lo: int = 0, root_hi
     st = tm_run_stats()
     _check(lib().tm_count(g, tr, ctypes.byref(a), pc, ctypes.byref(st) if stats else None, _stream(stream)))
     return (out, st.as_dict()) if stats else out
+
+
+def tm_count_noalloc(g, tr, counts, roots=None, root_lo: int = 0, root_hi: int = 0, stream=None):
+    """Allocation-free count into the device tensor ``counts`` (int64, n_motifs).
+
+    ``roots``: a CUDA int32 tensor of root edge ids, or None for the range.
+    The call does not synchronise; it allocates no device memory (its
+    scratch is a static array in the library, shared by all calls).
+    """
+    pc, on_dev, keep_c = _ptr(counts, np.int64)
+    if not on_dev:
+        raise TypeError("counts must be a CUDA tensor")
+    pr, n = None, 0
+    if roots is not None:
+        pr, r_dev, keep_r = _ptr(roots, np.int32)
+        if not r_dev:
+            raise TypeError("roots must be a CUDA tensor")
+        n = len(keep_r)
+    _check(lib().tm_count_noalloc(g, tr, pr, n, root_lo, root_hi, pc, _stream(stream)))
+    return counts
 
 
 # ------------------------------------------------------------------ handles
