@@ -305,6 +305,21 @@ __global__ void k_pair_insert(const int32_t *starts, int64_t n_pairs, int64_t n,
     atomicOr(bad, 4);
 }
 
+// pr_pos[e] = position of e in pair order; pr_end[e] = end of its run
+__global__ void k_pair_pos(const int32_t *pe, int64_t n, const int32_t *starts, int64_t n_pairs,
+                           int32_t *pr_pos, int32_t *pr_end) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int64_t lo = 0, hi = n_pairs;      // last run start <= i
+    while (hi - lo > 1) {
+        int64_t mid = (lo + hi) >> 1;
+        if (starts[mid] <= i) lo = mid; else hi = mid;
+    }
+    int32_t e = pe[i];
+    pr_pos[e] = (int32_t)i;
+    pr_end[e] = (int32_t)(lo + 1 < n_pairs ? starts[lo + 1] : n);
+}
+
 __global__ void k_fill_u64(unsigned long long *p, int64_t n, unsigned long long v) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) p[i] = v;
@@ -491,11 +506,15 @@ static int graph_build_impl(const int32_t *src_in, const int32_t *dst_in, const 
     TM_TRY(keep(g, &tab, (int64_t)cap));
     k_fill_u64<<<grid(2 * (int64_t)cap), 256, 0, s>>>((unsigned long long *)tab, 2 * (int64_t)cap, kEmptyKey);
     TM_CUDA_TRY(cudaGetLastError());
+    int32_t *pr_pos, *pr_end;
+    TM_TRY(keep(g, &pr_pos, E));
+    TM_TRY(keep(g, &pr_end, E));
     if (n_pairs > 0) {
         int32_t *starts;
         TM_TRY(sc.get(&starts, n_pairs));
         k_pair_compact<<<grid(E), 256, 0, s>>>(flag, pos, E, starts);
         k_pair_insert<<<grid(n_pairs), 256, 0, s>>>(starts, n_pairs, E, pair_eid, src, dst, tab, cap - 1, bad);
+        k_pair_pos<<<grid(E), 256, 0, s>>>(pair_eid, E, starts, n_pairs, pr_pos, pr_end);
         TM_CUDA_TRY(cudaGetLastError());
     }
     unsigned long long *mx;
@@ -515,6 +534,8 @@ static int graph_build_impl(const int32_t *src_in, const int32_t *dst_in, const 
     d.out_adj = out_adj;
     d.in_adj = in_adj;
     d.pair_eid = pair_eid;
+    d.pr_pos = pr_pos;
+    d.pr_end = pr_end;
     d.pair_tab = tab;
     d.pair_mask = cap - 1;
     g->n_pairs = n_pairs;

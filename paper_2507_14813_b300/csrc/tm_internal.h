@@ -43,6 +43,8 @@ struct DevGraph {
     const int64_t *in_off;    // V + 1
     const int2 *in_adj;       // (src, eid) grouped by dst
     const int32_t *pair_eid;  // eids ordered by (src, dst, eid)
+    const int32_t *pr_pos;    // by eid: position of the edge in pair_eid
+    const int32_t *pr_end;    // by eid: end of its (src, dst) run in pair_eid
     const ulonglong2 *pair_tab; // open-addressing table: x = key (src<<32|dst), y = start | len<<32
     uint64_t pair_mask;       // table capacity - 1 (power of two)
 };
@@ -76,7 +78,10 @@ static constexpr int kMaxE = TM_MAX_EDGES;
 static constexpr int kMaxV = TM_MAX_VERTICES;
 
 // Node flags
-static constexpr uint8_t kNodeParLeaf = 1;  // last level counted from the previous level's survivors
+static constexpr uint8_t kNodeParLeaf = 1;   // last level counted from the previous level's survivors
+static constexpr uint8_t kNodeStarLeaf = 2;  // ... and that last edge extends the same list as the level
+                                             //     before it (a star: same mapped centre, new other end)
+static constexpr uint8_t kNodeStarKids = 4;  // some single-edge leaf child has kNodeStarLeaf
 
 struct DevNode {
     int8_t k_begin;          // first level owned by this node (= |C_parent|)

@@ -64,7 +64,7 @@ struct __align__(16) Task {
     int16_t node;
     int8_t k;
     int8_t pad0;
-    int32_t pad1[2];
+    int64_t wend;             // end of the level's whole window (beyond the slice)
     int32_t eid[kMaxE];
     int64_t lo, hi;
 };
@@ -113,6 +113,9 @@ struct WarpState {
     int16_t sib_end[kMaxE];
     int8_t ltype[kMaxE];
     int8_t seq[kMaxE];        // survivors of level k are descended (not only counted)
+    int8_t star[kMaxE];       // suf[k] is kept (star leaves are counted from level k)
+    int64_t wend[kMaxE];      // end of level k's window (a donated slice may end earlier)
+    int64_t suf[kMaxE];       // survivors of level k from the current chunk to wend
     int32_t m2g[kMaxV];
     int32_t ehi[TM_MAX_DELTAS];
 };
@@ -228,6 +231,25 @@ __device__ int64_t pair_count(const DevGraph &g, int32_t x, int32_t w, int32_t l
 __device__ __forceinline__ int vload(const int *p) { return *(volatile const int *)p; }
 __device__ __forceinline__ unsigned int vloadu(const unsigned int *p) { return *(volatile const unsigned int *)p; }
 
+// Entries after position p of a run in ascending order (ending at `end`)
+// that are <= hi, given a[p] <= hi: galloping search from p.
+__device__ __forceinline__ int64_t run_tail(const int32_t *__restrict__ a, int64_t p, int64_t end, int32_t hi,
+                                            unsigned long long &probes) {
+    int64_t lo = p, step = 1, hi_pos = end;
+    while (true) {
+        int64_t q = lo + step;
+        if (q >= end) break;
+        probes++;
+        if (__ldg(a + q) <= hi) { lo = q; step <<= 1; } else { hi_pos = q; break; }
+    }
+    while (hi_pos - lo > 1) {
+        int64_t mid = lo + ((hi_pos - lo) >> 1);
+        probes++;
+        if (__ldg(a + mid) <= hi) lo = mid; else hi_pos = mid;
+    }
+    return lo - p;
+}
+
 template <bool kStats>
 struct Miner {
     const Params &p;
@@ -313,13 +335,31 @@ struct Miner {
     }
 
     // Leaf node L's last level for all survivor lanes S of level k, one ref at a time.
+    // A star leaf whose window is the frame's own counts from the frame:
+    // the later survivors of level k (suffix count `suf` of the chunk) minus
+    // the later edges of the lane's own (src, dst) run inside the window.
     __device__ void leaf_batch(const DevNode &L, int k, uint32_t S, int uk, int vk, int32_t cs, int32_t cd,
-                               int32_t last) {
+                               int32_t last, int frame_dmax, int64_t suf) {
+        const bool star = (L.flags & kNodeStarLeaf) && ws.star[k];
+        const uint32_t le = (lane == 31) ? 0xffffffffu : ((2u << lane) - 1u);   // lanes <= this one
         for (int i = 0; i < L.n_ref; i++) {
             const DevRef ref = p.tr.refs[L.ref_begin + i];
             const int32_t hi = ws.ehi[ref.delta];
             unsigned long long c = 0;
-            if (((S >> lane) & 1u) && last < hi) c = (unsigned long long)leaf_count(L, k + 1, uk, vk, cs, cd, last, hi);
+            if (((S >> lane) & 1u) && last < hi) {
+                if (star && ref.delta == frame_dmax) {
+                    unsigned long long pr = 0;
+                    const int64_t later = suf - __popc(S & le);
+                    const int64_t same = run_tail(p.g.pair_eid, __ldg(p.g.pr_pos + last), __ldg(p.g.pr_end + last), hi, pr);
+                    c = (unsigned long long)(later - same);
+                    if (kStats) {
+                        w.v[kStPairProbe] += pr + 2;
+                        w.v[kStLeaf] += 1;
+                    }
+                } else {
+                    c = (unsigned long long)leaf_count(L, k + 1, uk, vk, cs, cd, last, hi);
+                }
+            }
             c = warp_sum_u64(c);
             if (lane == 0) add_count(ref.counter, c);
         }
@@ -328,7 +368,7 @@ struct Miner {
     // Chunk-level work for survivors S of level k of node N: count the refs
     // of a completed node, count single-edge leaves lane-parallel; returns
     // the survivors to descend.
-    __device__ uint32_t survivors(int k, const DevNode &N, uint32_t S, int2 c) {
+    __device__ uint32_t survivors(int k, const DevNode &N, uint32_t S, int2 c, int64_t suf) {
         if (S == 0) return 0;
         const int uk = N.eu[k], vk = N.ev[k];
         int32_t cs, cd;
@@ -352,13 +392,13 @@ struct Miner {
             for (int ci = 0; ci < N.n_par; ci++) {
                 const DevNode L = p.tr.nodes[N.child_begin + N.n_seq + ci];
                 uint32_t S2 = __ballot_sync(0xffffffffu, c.y < ws.ehi[L.dmax]) & S;
-                if (S2) leaf_batch(L, k, S2, uk, vk, cs, cd, c.y);
+                if (S2) leaf_batch(L, k, S2, uk, vk, cs, cd, c.y, N.dmax, suf);
             }
         }
         const bool par_self = (N.flags & kNodeParLeaf) && (k == N.k_end - 2);
         if (par_self) {
             uint32_t S2 = __ballot_sync(0xffffffffu, c.y < ws.ehi[N.dmax]) & S;
-            if (S2) leaf_batch(N, k, S2, uk, vk, cs, cd, c.y);
+            if (S2) leaf_batch(N, k, S2, uk, vk, cs, cd, c.y, N.dmax, suf);
         }
         return ws.seq[k] ? S : 0u;
     }
@@ -384,7 +424,8 @@ struct Miner {
         return complete ? (N.n_seq > 0) : !par_self;
     }
 
-    __device__ void set_frame(int k, int node, int sib_end, int8_t lt, int32_t x, int64_t pos, int64_t end, bool seq) {
+    __device__ void set_frame(int k, int node, int sib_end, int8_t lt, int32_t x, int64_t pos, int64_t end, bool seq,
+                              int64_t wend, bool star, int64_t suf) {
         __syncwarp();
         if (lane == 0) {
             ws.node[k] = (int16_t)node;
@@ -395,8 +436,40 @@ struct Miner {
             ws.end[k] = end;
             ws.mask[k] = 0;
             ws.seq[k] = seq ? 1 : 0;
+            ws.wend[k] = wend;
+            ws.star[k] = star ? 1 : 0;
+            ws.suf[k] = suf;
         }
         __syncwarp();
+    }
+
+    // Star leaves are counted from level k of node N.
+    __device__ __forceinline__ bool star_of(const DevNode &N, int k) const {
+        return ((N.flags & kNodeStarLeaf) && (N.flags & kNodeParLeaf) && k == N.k_end - 2) ||
+               ((N.flags & kNodeStarKids) && k == N.k_end - 1);
+    }
+
+    // Survivors of level k of node N in [pos, wend) (the filter of load_chunk).
+    __device__ int64_t count_survivors(const DevNode &N, int k, int8_t lt, int64_t pos, int64_t wend) {
+        const int2 *adj = lt == kListOut ? p.g.out_adj : p.g.in_adj;
+        const int32_t last = ws.eid[k - 1];
+        const int32_t hi = ws.ehi[N.dmax];
+        const int nv = N.nvb[k];
+        int64_t n = 0;
+        for (int64_t b = pos; b < wend; b += 32) {
+            const int64_t i = b + lane;
+            bool ok = false;
+            if (i < wend) {
+                const int2 c = __ldg(adj + i);
+                bool bad = false;
+#pragma unroll
+                for (int l = 0; l < kMaxV; l++) bad |= (l < nv) & (c.x == ws.m2g[l]);
+                ok = !bad && c.y > last && c.y <= hi;
+            }
+            n += __popc(__ballot_sync(0xffffffffu, ok));
+            if (kStats && lane == 0) w.v[kStCand] += (unsigned long long)((wend - b) < 32 ? (wend - b) : 32);
+        }
+        return n;
     }
 
     // Open level k for node `node` (siblings up to sib_end): the slice of
@@ -421,7 +494,9 @@ struct Miner {
             else start = warp_upper(adj, b0, b1, last, lane, w.v[kStListProbe]);
             end = (b1 - start <= 32) ? b1 : warp_upper(adj, start, b1, hi, lane, w.v[kStListProbe]);
         }
-        set_frame(k, node, sib_end, lt, x, start, end, seq_of(N, k));
+        const bool star = lt != kListGlobal && star_of(N, k);
+        const int64_t suf = star ? count_survivors(N, k, lt, start, end) : 0;
+        set_frame(k, node, sib_end, lt, x, start, end, seq_of(N, k), end, star, suf);
         if (kStats && lane == 0) w.v[kStExp]++;
     }
 
@@ -455,6 +530,7 @@ struct Miner {
                 tk->k = (int8_t)kb;
                 tk->lo = mid;
                 tk->hi = end;
+                tk->wend = ws.wend[kb];
                 ws.end[kb] = mid;
             }
             __threadfence();
@@ -499,6 +575,7 @@ struct Miner {
         for (int i = 0; i < kMaxE; i++) tk.eid[i] = src->eid[i];
         tk.lo = src->lo;
         tk.hi = src->hi;
+        tk.wend = src->wend;
         return true;
     }
 
@@ -584,12 +661,14 @@ struct Miner {
         const uint32_t VB = __ballot_sync(0xffffffffu, valid);
         if (kStats && lane == 0) w.v[kStCand] += (unsigned long long)__popc(VB);
         ws.cand[k][lane] = c;
+        const int64_t suf = ws.suf[k];
         __syncwarp();
         if (lane == 0) {
             ws.cbase[k] = base;
             ws.pos[k] = outw ? end : base + 32;
+            ws.suf[k] = suf - __popc(S);
         }
-        uint32_t D = survivors(k, N, S, c);
+        uint32_t D = survivors(k, N, S, c, suf);
         __syncwarp();
         if (lane == 0) ws.mask[k] = D;
         __syncwarp();
@@ -653,13 +732,13 @@ struct Miner {
         if (a == b) return;                             // injective map needs a != b
         windows(r);
         const DevNode N0 = p.tr.nodes[0];
-        set_frame(0, 0, 1, kListGlobal, -1, 0, 0, seq_of(N0, 0));
+        set_frame(0, 0, 1, kListGlobal, -1, 0, 0, seq_of(N0, 0), 0, false, 0);
         if (lane == 0) ws.cbase[0] = r;
         // level 0: the root edge as a one-candidate chunk on lane 0
         int2 c = make_int2(lane == 0 ? b : 0, lane == 0 ? r : 0);
         ws.cand[0][lane] = c;
         __syncwarp();
-        uint32_t D = survivors(0, N0, 1u, c);
+        uint32_t D = survivors(0, N0, 1u, c, 0);
         __syncwarp();
         if (lane == 0) ws.mask[0] = D;
         __syncwarp();
@@ -684,7 +763,9 @@ struct Miner {
         int8_t lt;
         int32_t x;
         list_of(N, k, lt, x);
-        set_frame(k, tk.node, tk.node + 1, lt, x, tk.lo, tk.hi, seq_of(N, k));
+        const bool star = lt != kListGlobal && star_of(N, k);
+        const int64_t suf = star ? count_survivors(N, k, lt, tk.lo, tk.wend) : 0;
+        set_frame(k, tk.node, tk.node + 1, lt, x, tk.lo, tk.hi, seq_of(N, k), tk.wend, star, suf);
         run(k);
     }
 };

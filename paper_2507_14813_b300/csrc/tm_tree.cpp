@@ -232,6 +232,19 @@ void flatten(const HostTree &h, bool par_leaves, TreeImage *img) {
         const Edge &e = nd.C[m - 1];
         return e.first < nvb || e.second < nvb;   // connected last edge
     };
+    // The last edge extends the same candidate list as the edge before it
+    // (same mapped centre, new far end), so its candidates are the later
+    // entries of that list minus the new vertex's own repeats.
+    auto is_star = [&](int i) {
+        const HostNode &nd = h.nodes[i];
+        int m = (int)nd.C.size();
+        if (m < 2) return false;
+        const Edge &e2 = nd.C[m - 2], &e1 = nd.C[m - 1];
+        int nv2 = nvb_of(nd.C, m - 2), nv1 = nvb_of(nd.C, m - 1);
+        bool out = e2.first < nv2 && e2.second >= nv2 && e1.first == e2.first && e1.second >= nv1;
+        bool in = e2.second < nv2 && e2.first >= nv2 && e1.second == e2.second && e1.first >= nv1;
+        return out || in;
+    };
     // BFS order with seq children before par children
     std::vector<int> order;
     std::vector<int> newid(nn, -1);
@@ -260,6 +273,9 @@ void flatten(const HostTree &h, bool par_leaves, TreeImage *img) {
         dn.k_begin = (int8_t)(nd.parent >= 0 ? h.nodes[nd.parent].C.size() : 0);
         dn.k_end = (int8_t)m;
         dn.flags = is_par(i) ? kNodeParLeaf : 0;
+        if (is_par(i) && is_star(i)) dn.flags |= kNodeStarLeaf;
+        for (int32_t c : nd.children)
+            if (is_par(c) && is_star(c) && h.nodes[c].C.size() == nd.C.size() + 1) dn.flags |= kNodeStarKids;
         dn.dmax = (int8_t)std::max(dmax[i], 0);
         dn.parent = (int16_t)(nd.parent >= 0 ? newid[nd.parent] : -1);
         int n_par = 0, n_seq = 0;

@@ -270,3 +270,18 @@ def test_mid_config_heavy_roots_split(mid):
     s3 = tmotif.count(g, tr3, roots=roots)
     d3 = tmotif.count(g, tr3, roots=roots, mode=D)
     assert s3.tolist() == d3.tolist() == [a[i] for i, m in enumerate(synth.CONFIG2_MOTIFS) if len(m) == 3]
+
+
+def test_mid_config_heavy_star_leaves_vs_scan(mid):
+    """Star leaves (out- and in-stars) on heavy roots: counting from the
+    level's survivor suffix and the edge's own pair run must equal the scan,
+    with subtrees split across warps."""
+    src, dst, t, g = mid
+    roots = synth.root_sample(24, len(src), 32)
+    ms = [((0, 1), (0, 2), (0, 3)), ((0, 1), (2, 1), (3, 1)), ((0, 1), (0, 2)), ((0, 1), (2, 1)),
+          ((0, 1), (1, 2), (1, 3))]
+    tr = tmotif.Tree(ms, [synth.MID_DELTA, synth.MID_DELTA, 1800, 3600, 900])
+    a, st = tmotif.count(g, tr, roots=roots, mode=D, stats=True)
+    b = tmotif.count(g, tr, roots=roots, mode=D | tmotif.TM_LEAF_SCAN)
+    assert a.tolist() == b.tolist()
+    assert st["tasks_split"] > 0
