@@ -136,6 +136,7 @@ int tm_tree_free(tm_tree *tr);
 #define TM_PERMOTIF 0x1u      /* one chain per distinct motif, one launch each (Algorithm 1) */
 #define TM_LEAF_SCAN 0x10u    /* count a leaf's last edge by scanning its window only */
 #define TM_SCHED_DYNAMIC 0x100u /* persistent launch, heavy subtrees split across warps */
+#define TM_SCHED_PLANNED 0x200u /* persistent launch; cut root i's first-level lists into root_split[i] slices */
 
 /* flags */
 #define TM_ROOTS_DEVICE 0x1u  /* roots points to device memory */
@@ -159,6 +160,7 @@ typedef struct {
     int64_t *per_root_work;   /* device, [n_roots][TM_WORK_FIELDS], or NULL; overwritten */
     int32_t ctas_per_sm;      /* 0: library default */
     int32_t reserved;
+    const int32_t *root_split; /* device, per root: slices for TM_SCHED_PLANNED (<= 1: none), or NULL */
 } tm_count_args;
 
 typedef struct {
@@ -224,6 +226,58 @@ int tm_count(const tm_graph *g, const tm_tree *tr, const tm_count_args *args, in
  */
 int tm_count_noalloc(const tm_graph *g, const tm_tree *tr, const int32_t *roots, int64_t n_roots,
                      int64_t root_lo, int64_t root_hi, int64_t *counts, void *stream);
+
+/* ------------------------------------------------------------ learned scheduling */
+/*
+ * A small cost model predicts each root edge's search cost so the launch can
+ * start the heaviest roots first and cut them into slices for other warps.
+ * The paper has no learned part (its GPU runtime rebalances reactively,
+ * Section 4.5); this follows the scheduling scheme the library adds on top.
+ *
+ * Features (tm_features), TM_FEATURES float32 per root, each log1p-scaled:
+ * out- and in-degree of the root's destination, out-degree of its source,
+ * the number of entries of those three lists inside the root's window (the
+ * tree's largest delta), the tree's depth and the root node's fan-out.
+ * Model: TM_FEATURES -> 64 -> 64 -> 1, ReLU, standardised inputs, FP16
+ * weights and FP32 accumulation on the device, FP32 master weights for
+ * training (Adam, mean squared error).  Parameters in one float32 vector:
+ * W1 (64 x 8, row-major), b1 (64), W2 (64 x 64), b2 (64), W3 (64), b3 (1).
+ * Labels are log1p of measured work (tm_count's per-root work counters:
+ * candidates + probes).  All pointers to features, labels, predictions and
+ * plans are device pointers; the calls that do not say otherwise do not
+ * synchronise `stream`.
+ */
+#define TM_FEATURES 8
+#define TM_MODEL_PARAMS 4801
+
+typedef struct tm_model tm_model;   /* opaque, library-owned, device resident */
+
+int tm_features(const tm_graph *g, const tm_tree *tr, const int32_t *roots, int64_t n_roots, float *feats,
+                void *stream);
+/* He-initialised weights from `seed`; synchronises the device. */
+int tm_model_create(uint64_t seed, tm_model **out);
+int tm_model_free(tm_model *m);
+/* Host copies of the FP32 parameters (TM_MODEL_PARAMS) and of the input
+ * standardisation (mean[8] then inverse std[8]); either pointer may be NULL. */
+int tm_model_get_params(const tm_model *m, float *params, float *norm);
+int tm_model_set_params(tm_model *m, const float *params, const float *norm);
+/* Input standardisation from n feature rows. */
+int tm_model_fit_norm(tm_model *m, const float *feats, int64_t n, void *stream);
+/* Predicted log1p(work) of n rows into out. */
+int tm_model_predict(const tm_model *m, const float *feats, int64_t n, float *out, void *stream);
+/* Mean squared error and its gradient over n rows at the current weights
+ * (host outputs, TM_MODEL_PARAMS gradients; either may be NULL); synchronises. */
+int tm_model_loss_grad(const tm_model *m, const float *feats, const float *labels, int64_t n, float *loss,
+                       float *grad, void *stream);
+/* Adam over contiguous minibatches for `epochs` passes; loss_history
+ * (host, epochs floats, may be NULL) gets each pass's mean loss; synchronises. */
+int tm_model_train(tm_model *m, const float *feats, const float *labels, int64_t n, int32_t epochs, int32_t batch,
+                   float lr, float *loss_history, void *stream);
+/* Plan: roots_out = roots ordered by decreasing predicted work; split_out[i] =
+ * number of slices (1..max_split) for root roots_out[i], about one slice per
+ * unit_work of predicted work.  Pass both to tm_count with TM_SCHED_PLANNED. */
+int tm_plan(const tm_model *m, const float *feats, const int32_t *roots, int64_t n, double unit_work,
+            int32_t max_split, int32_t *roots_out, int32_t *split_out, void *stream);
 
 /* Message describing the last error on the calling thread ("" if none). */
 const char *tm_last_error(void);

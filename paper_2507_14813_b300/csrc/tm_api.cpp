@@ -115,7 +115,10 @@ int tm_count(const tm_graph *g, const tm_tree *tr, const tm_count_args *args, in
              void *stream) {
     g_last_error.clear();
     if (!g || !tr || !args || !counts) { set_error("tm_count: NULL argument"); return TM_EINVAL; }
-    if (args->mode & ~(TM_PERMOTIF | TM_LEAF_SCAN | TM_SCHED_DYNAMIC)) { set_error("tm_count: unknown mode bit"); return TM_EINVAL; }
+    if (args->mode & ~(TM_PERMOTIF | TM_LEAF_SCAN | TM_SCHED_DYNAMIC | TM_SCHED_PLANNED)) {
+        set_error("tm_count: unknown mode bit");
+        return TM_EINVAL;
+    }
     if (args->flags & ~(TM_ROOTS_DEVICE | TM_COUNTS_DEVICE)) { set_error("tm_count: unknown flag"); return TM_EINVAL; }
     if (args->roots && args->n_roots < 0) { set_error("tm_count: n_roots < 0"); return TM_EINVAL; }
     return mine(g, tr, args, counts, stats, (cudaStream_t)stream);

@@ -370,6 +370,31 @@ unsigned grid(int64_t n, int b = 256) { return (unsigned)std::max<int64_t>(1, cd
 
 }  // namespace
 
+// Stable sort of (uint32 key, int32 value) pairs by the low `bits` bits of the
+// key; the result is left in (keys, vals).
+int sort_u32_pairs(uint32_t *keys, int32_t *vals, int64_t n, int bits, cudaStream_t s) {
+    if (n <= 1) return TM_OK;
+    uint32_t *k2 = nullptr;
+    int32_t *v2 = nullptr;
+    TM_CUDA_TRY(cudaMallocAsync((void **)&k2, sizeof(uint32_t) * n, s));
+    cudaError_t e = cudaMallocAsync((void **)&v2, sizeof(int32_t) * n, s);
+    if (e != cudaSuccess) {
+        cudaFreeAsync(k2, s);
+        set_error("sort: allocation");
+        return TM_ENOMEM;
+    }
+    uint32_t *ka = keys, *kb = k2;
+    int32_t *va = vals, *vb = v2;
+    int rc = radix_sort<uint32_t>(&ka, &va, &kb, &vb, n, bits, s);
+    if (rc == TM_OK && ka != keys) {
+        cudaMemcpyAsync(keys, ka, sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, s);
+        cudaMemcpyAsync(vals, va, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, s);
+    }
+    cudaFreeAsync(k2, s);
+    cudaFreeAsync(v2, s);
+    return rc;
+}
+
 void graph_release(tm_graph *g) {
     if (!g) return;
     for (void *p : g->allocs) cudaFree(p);

@@ -95,7 +95,9 @@ struct Params {
     unsigned long long *stats;        // kStatFields totals or null
     int32_t chunk;                    // roots claimed per cursor step
     int32_t smem_counters;            // 1: per-CTA counters in shared memory
-    int32_t dynamic;                  // 1: persistent launch with task donation
+    int32_t dynamic;                  // 1: persistent launch with a task queue
+    int32_t react;                    // 1: warps donate slices when others are idle
+    const int32_t *split;             // per root index: slices for its first-level lists, or null
 };
 
 enum { kStCand = 0, kStExp, kStListProbe, kStHashProbe, kStPairProbe, kStLeaf, kStRoots, kStSplit, kStatFields };
@@ -259,9 +261,10 @@ struct Miner {
     Work w;
     int64_t ri;                        // root index of the current work (per-root outputs)
     int polls;                         // chunk loads since the last look at the idle counter
+    int split_h;                       // planned slices for the current root's first-level lists
 
     __device__ Miner(const Params &pp, WarpState &s, unsigned long long *c, int l)
-        : p(pp), ws(s), s_cnt(c), lane(l), polls(0) {
+        : p(pp), ws(s), s_cnt(c), lane(l), polls(0), split_h(0) {
         for (int i = 0; i < kStatFields; i++) w.v[i] = 0;
     }
 
@@ -498,9 +501,53 @@ struct Miner {
         const int64_t suf = star ? count_survivors(N, k, lt, start, end) : 0;
         set_frame(k, node, sib_end, lt, x, start, end, seq_of(N, k), end, star, suf);
         if (kStats && lane == 0) w.v[kStExp]++;
+        if (k == 1 && split_h > 1) force_split(k, split_h);
+    }
+
+    // Planned split: cut the unscanned part of level k into `parts` slices of
+    // whole chunks, keep the first, queue the rest.
+    __device__ void force_split(int k, int parts) {
+        const int64_t pos = ws.pos[k], end = ws.end[k];
+        const int64_t rem = end - pos;
+        if (rem <= 32) return;
+        int64_t sz = (rem + parts - 1) / parts;
+        sz = (sz + 31) & ~31ll;
+        for (int64_t lo = pos + sz; lo < end; lo += sz)
+            if (!push_task(k, lo, min(end, lo + sz))) return;
+        __syncwarp();
+        if (lane == 0) ws.end[k] = pos + sz;
+        __syncwarp();
     }
 
     // ---------------------------------------------------------------- tasks
+
+    // Publish the slice [lo, hi) of level k under the current partial match;
+    // false when the queue is full (the caller keeps the work).
+    __device__ bool push_task(int k, int64_t lo, int64_t hi) {
+        unsigned int slot = 0;
+        if (lane == 0) slot = atomicAdd(&p.q->tail, 1u);
+        slot = __shfl_sync(0xffffffffu, slot, 0);
+        if (slot >= (unsigned int)kQueueCap) return false;
+        Task *tk = p.tasks + slot;
+        if (lane < kMaxE) tk->eid[lane] = lane < k ? ws.eid[lane] : -1;
+        if (lane == 0) {
+            tk->ri = (int32_t)ri;
+            tk->node = ws.node[k];
+            tk->k = (int8_t)k;
+            tk->lo = lo;
+            tk->hi = hi;
+            tk->wend = ws.wend[k];
+        }
+        __threadfence();
+        __syncwarp();
+        if (lane == 0) {
+            __threadfence();
+            atomicExch(p.ready + slot, 1);
+        }
+        if (kStats && lane == 0) w.v[kStSplit]++;
+        __syncwarp();
+        return true;
+    }
 
     // Hand [mid, end) of the shallowest long slice in levels [kbase, top] to the queue.
     __device__ void maybe_donate(int kbase, int top) {
@@ -518,29 +565,11 @@ struct Miner {
             const int64_t rem = end - pos;
             if (rem < (ws.seq[kb] ? kDonateSeq : kDonateLeaf)) continue;
             const int64_t mid = pos + (((rem >> 1) + 31) & ~31ll);
-            unsigned int slot = 0;
-            if (lane == 0) slot = atomicAdd(&p.q->tail, 1u);
-            slot = __shfl_sync(0xffffffffu, slot, 0);
-            if (slot >= (unsigned int)kQueueCap) return;      // full: keep the work
-            Task *tk = p.tasks + slot;
-            if (lane < kMaxE) tk->eid[lane] = lane < kb ? ws.eid[lane] : -1;
-            if (lane == 0) {
-                tk->ri = (int32_t)ri;
-                tk->node = ws.node[kb];
-                tk->k = (int8_t)kb;
-                tk->lo = mid;
-                tk->hi = end;
-                tk->wend = ws.wend[kb];
-                ws.end[kb] = mid;
+            if (push_task(kb, mid, end)) {
+                __syncwarp();
+                if (lane == 0) ws.end[kb] = mid;
+                __syncwarp();
             }
-            __threadfence();
-            __syncwarp();
-            if (lane == 0) {
-                __threadfence();
-                atomicExch(p.ready + slot, 1);
-            }
-            if (kStats && lane == 0) w.v[kStSplit]++;
-            __syncwarp();
             return;
         }
     }
@@ -710,7 +739,7 @@ struct Miner {
                 continue;
             }
             if (ws.pos[k] < ws.end[k]) {
-                if (p.dynamic && ++polls >= kPollEvery) {
+                if (p.react && ++polls >= kPollEvery) {
                     polls = 0;
                     maybe_donate(kbase, k);
                 }
@@ -785,7 +814,7 @@ __device__ void flush_work(Miner<kStats> &M, const Work &before, const Params &p
 }
 
 template <bool kStats>
-__global__ void __launch_bounds__(kThreads) k_mine(Params p) {
+__global__ void __launch_bounds__(kThreads, 4) k_mine(Params p) {
     extern __shared__ unsigned long long s_cnt[];
     __shared__ WarpState s_ws[kWarps];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -799,6 +828,7 @@ __global__ void __launch_bounds__(kThreads) k_mine(Params p) {
             Task tk;
             if (M.pop(tk)) {
                 M.ri = tk.ri;
+                M.split_h = 0;
                 Work before = M.w;
                 M.task(tk);
                 flush_work(M, before, p, lane);
@@ -812,6 +842,7 @@ __global__ void __launch_bounds__(kThreads) k_mine(Params p) {
             const int64_t last = min((int64_t)first + p.chunk, p.n_roots);
             for (int64_t ri = (int64_t)first; ri < last; ri++) {
                 M.ri = ri;
+                M.split_h = p.split ? __ldg(p.split + ri) : 0;
                 const int32_t r = p.roots ? __ldg(p.roots + ri) : (int32_t)(p.root_lo + ri);
                 Work before = M.w;
                 M.root(r);
@@ -846,7 +877,13 @@ int mine(const tm_graph *g, const tm_tree *tr, const tm_count_args *args, int64_
     const int n_motifs = tr->h.n_motifs;
     const bool comine = (args->mode & TM_PERMOTIF) == 0;
     const bool par = (args->mode & TM_LEAF_SCAN) == 0;
-    const bool dynamic = (args->mode & TM_SCHED_DYNAMIC) != 0;
+    const bool react = (args->mode & TM_SCHED_DYNAMIC) != 0;
+    const bool planned = (args->mode & TM_SCHED_PLANNED) != 0;
+    const bool dynamic = react || planned;
+    if (planned && !args->root_split) {
+        set_error("tm_count: TM_SCHED_PLANNED needs root_split");
+        return TM_EINVAL;
+    }
     const bool want_stats = stats != nullptr;
     int64_t n_roots;
     if (args->roots) {
@@ -952,6 +989,8 @@ int mine(const tm_graph *g, const tm_tree *tr, const tm_count_args *args, int64_
         prm.chunk = chunk;
         prm.smem_counters = smem_cnt ? 1 : 0;
         prm.dynamic = dynamic ? 1 : 0;
+        prm.react = react ? 1 : 0;
+        prm.split = planned ? args->root_split : nullptr;
         if (dynamic && L == 0) cudaMemsetAsync(d_ready, 0, b_ready, s);
         kern<<<blocks, kThreads, dyn_smem, s>>>(prm);
         cudaError_t e = cudaGetLastError();
@@ -1122,6 +1161,8 @@ extern "C" int tm_count_noalloc(const tm_graph *g, const tm_tree *tr, const int3
         prm.chunk = (int32_t)std::max<int64_t>(1, std::min<int64_t>(16, n_roots / ((int64_t)blocks * kWarps * 64)));
         prm.smem_counters = 1;
         prm.dynamic = 0;
+        prm.react = 0;
+        prm.split = nullptr;
         k_mine<false><<<blocks, kThreads, dyn_smem, s>>>(prm);
         TM_CUDA_TRY(cudaGetLastError());
     }

@@ -33,6 +33,9 @@ TM_COMINE = 0x0
 TM_PERMOTIF = 0x1
 TM_LEAF_SCAN = 0x10
 TM_SCHED_DYNAMIC = 0x100
+TM_SCHED_PLANNED = 0x200
+TM_FEATURES = 8
+TM_MODEL_PARAMS = 4801
 
 TM_ROOTS_DEVICE = 0x1
 TM_COUNTS_DEVICE = 0x2
@@ -72,7 +75,7 @@ class tm_count_args(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_uint32), ("flags", ctypes.c_uint32), ("roots", ctypes.c_void_p),
                 ("n_roots", ctypes.c_int64), ("root_lo", ctypes.c_int64), ("root_hi", ctypes.c_int64),
                 ("per_root_counts", ctypes.c_void_p), ("per_root_work", ctypes.c_void_p),
-                ("ctas_per_sm", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("ctas_per_sm", ctypes.c_int32), ("reserved", ctypes.c_int32), ("root_split", ctypes.c_void_p)]
 
 
 class tm_run_stats(ctypes.Structure):
@@ -88,6 +91,8 @@ _lib = None
 
 EXPORTS = ("tm_graph_load", "tm_graph_get_info", "tm_graph_edges", "tm_graph_free", "tm_tree_build",
            "tm_tree_get_info", "tm_tree_get_node", "tm_tree_free", "tm_count", "tm_count_noalloc",
+           "tm_features", "tm_model_create", "tm_model_free", "tm_model_get_params", "tm_model_set_params",
+           "tm_model_fit_norm", "tm_model_predict", "tm_model_loss_grad", "tm_model_train", "tm_plan",
            "tm_last_error", "tm_version")
 
 
@@ -109,6 +114,17 @@ def lib():
         L.tm_tree_free.argtypes = [P]
         L.tm_count.argtypes = [P, P, ctypes.POINTER(tm_count_args), P, ctypes.POINTER(tm_run_stats), P]
         L.tm_count_noalloc.argtypes = [P, P, P, i64, i64, i64, P, P]
+        F = ctypes.c_float
+        L.tm_features.argtypes = [P, P, P, i64, P, P]
+        L.tm_model_create.argtypes = [ctypes.c_uint64, ctypes.POINTER(P)]
+        L.tm_model_free.argtypes = [P]
+        L.tm_model_get_params.argtypes = [P, P, P]
+        L.tm_model_set_params.argtypes = [P, P, P]
+        L.tm_model_fit_norm.argtypes = [P, P, i64, P]
+        L.tm_model_predict.argtypes = [P, P, i64, P, P]
+        L.tm_model_loss_grad.argtypes = [P, P, P, i64, P, P, P]
+        L.tm_model_train.argtypes = [P, P, P, i64, i32, i32, F, P, P]
+        L.tm_plan.argtypes = [P, P, P, i64, ctypes.c_double, i32, P, P, P]
         L.tm_last_error.restype = ctypes.c_char_p
         L.tm_version.restype = ctypes.c_char_p
         for name in EXPORTS:
@@ -229,7 +245,7 @@ def tm_tree_free(tr) -> None:
 
 def tm_count(g, tr, mode: int = TM_COMINE, roots=None, root_lo: int = 0, root_hi: int = 0,
              counts=None, per_root_counts=None, per_root_work=None, stats: bool = False,
-             stream=None, ctas_per_sm: int = 0):
+             stream=None, ctas_per_sm: int = 0, root_split=None):
     """Counts of every motif (np.int64 array, or into the device tensor ``counts``).
 
     Returns ``counts`` or ``(counts, stats_dict)`` when ``stats``.
@@ -255,6 +271,12 @@ def tm_count(g, tr, mode: int = TM_COMINE, roots=None, root_lo: int = 0, root_hi
             keep.append(k)
             setattr(a, name, p)
     a.ctas_per_sm = ctas_per_sm
+    if root_split is not None:
+        p, on_dev, k = _ptr(root_split, np.int32)
+        if not on_dev:
+            raise TypeError("root_split must be a CUDA tensor")
+        keep.append(k)
+        a.root_split = p
     n_motifs = tm_tree_get_info(tr)["n_motifs"]
     if counts is None:
         out = np.zeros(n_motifs, np.int64)
@@ -286,6 +308,87 @@ def tm_count_noalloc(g, tr, counts, roots=None, root_lo: int = 0, root_hi: int =
         n = len(keep_r)
     _check(lib().tm_count_noalloc(g, tr, pr, n, root_lo, root_hi, pc, _stream(stream)))
     return counts
+
+
+# ------------------------------------------------------------------ learned scheduling
+
+def _dev(x, dtype, name):
+    p, on_dev, k = _ptr(x, dtype)
+    if not on_dev:
+        raise TypeError(name + " must be a CUDA tensor")
+    return p
+
+
+def _devf(x, name):
+    import torch
+    if not (_is_torch(x) and x.is_cuda and x.dtype == torch.float32 and x.is_contiguous()):
+        raise TypeError(name + " must be a contiguous CUDA float32 tensor")
+    return ctypes.c_void_p(x.data_ptr())
+
+
+def tm_features(g, tr, roots, feats, stream=None):
+    n = len(roots)
+    _check(lib().tm_features(g, tr, _dev(roots, np.int32, "roots"), n, _devf(feats, "feats"), _stream(stream)))
+    return feats
+
+
+class Model:
+    """Owning wrapper of a tm_model (the scheduler's cost model)."""
+
+    def __init__(self, seed: int = 1):
+        self.h = ctypes.c_void_p()
+        _check(lib().tm_model_create(int(seed), ctypes.byref(self.h)))
+
+    def params(self):
+        w = np.zeros(TM_MODEL_PARAMS, np.float32)
+        nm = np.zeros(2 * TM_FEATURES, np.float32)
+        _check(lib().tm_model_get_params(self.h, w.ctypes.data_as(ctypes.c_void_p), nm.ctypes.data_as(ctypes.c_void_p)))
+        return w, nm
+
+    def set_params(self, w=None, norm=None):
+        pw = None if w is None else np.ascontiguousarray(w, np.float32)
+        pn = None if norm is None else np.ascontiguousarray(norm, np.float32)
+        _check(lib().tm_model_set_params(self.h, None if pw is None else pw.ctypes.data_as(ctypes.c_void_p),
+                                         None if pn is None else pn.ctypes.data_as(ctypes.c_void_p)))
+
+    def fit_norm(self, feats, stream=None):
+        _check(lib().tm_model_fit_norm(self.h, _devf(feats, "feats"), feats.shape[0], _stream(stream)))
+
+    def predict(self, feats, out, stream=None):
+        _check(lib().tm_model_predict(self.h, _devf(feats, "feats"), feats.shape[0], _devf(out, "out"),
+                                      _stream(stream)))
+        return out
+
+    def loss_grad(self, feats, labels, stream=None):
+        loss = ctypes.c_float(0)
+        g = np.zeros(TM_MODEL_PARAMS, np.float32)
+        _check(lib().tm_model_loss_grad(self.h, _devf(feats, "feats"), _devf(labels, "labels"), feats.shape[0],
+                                        ctypes.byref(loss), g.ctypes.data_as(ctypes.c_void_p), _stream(stream)))
+        return float(loss.value), g
+
+    def train(self, feats, labels, epochs: int, batch: int = 256, lr: float = 1e-3, stream=None):
+        hist = np.zeros(max(epochs, 1), np.float32)
+        _check(lib().tm_model_train(self.h, _devf(feats, "feats"), _devf(labels, "labels"), feats.shape[0],
+                                    int(epochs), int(batch), float(lr), hist.ctypes.data_as(ctypes.c_void_p),
+                                    _stream(stream)))
+        return hist[:epochs]
+
+    def plan(self, feats, roots, roots_out, split_out, unit_work: float, max_split: int, stream=None):
+        _check(lib().tm_plan(self.h, _devf(feats, "feats"), _dev(roots, np.int32, "roots"), len(roots),
+                             float(unit_work), int(max_split), _dev(roots_out, np.int32, "roots_out"),
+                             _dev(split_out, np.int32, "split_out"), _stream(stream)))
+        return roots_out, split_out
+
+    def close(self):
+        if getattr(self, "h", None) is not None and _lib is not None:
+            _check(lib().tm_model_free(self.h))
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 # ------------------------------------------------------------------ handles
