@@ -32,6 +32,8 @@ WORKLOADS = {
     # name: (graph spec, motifs, delta, default root sample)
     "mid": ("MID", "CONFIG2_MOTIFS", 3600, 64),
     "tiny": ("TINY", "CONFIG1_MOTIFS", 10_000, 50_000),
+    "batched": (None, None, None, 65536),
+    "serving": (None, None, None, 64),
 }
 
 
@@ -131,6 +133,209 @@ def cpu_baseline(src, dst, t, motifs, delta, roots, seconds=20.0, threads=1):
     return value, done_min
 
 
+def learned_schedule(args, tmotif, g, tr, src, rank, d_roots, counts, ref_counts, stream, flush, mode):
+    """Train the cost model on measured per-root work of a separate sample,
+    plan the benchmark's roots by it, and time the planned launch."""
+    import torch
+    from paper_2507_14813_b300 import synth
+    n_train = args.train_roots
+    t0 = time.perf_counter()
+    train = torch.from_numpy(synth.root_sample(200 + rank, len(src), n_train)).cuda()
+    work = torch.zeros((n_train, tmotif.TM_WORK_FIELDS), dtype=torch.int64, device="cuda")
+    tmotif.tm_count(g.h, tr.h, roots=train, per_root_work=work, mode=tmotif.TM_SCHED_DYNAMIC, stats=True)
+    w = work.cpu().numpy()
+    y = torch.from_numpy(np.log1p(w[:, 0] + w[:, 2]).astype(np.float32)).cuda()
+    X = torch.zeros((n_train, tmotif.TM_FEATURES), dtype=torch.float32, device="cuda")
+    tmotif.tm_features(g.h, tr.h, train, X)
+    model = tmotif.Model(seed=1)
+    model.fit_norm(X)
+    hist = model.train(X, y, epochs=120, batch=256, lr=3e-3)
+    t_train = time.perf_counter() - t0
+    # prediction error on the benchmark's own roots, judged by their measured work
+    R = len(d_roots)
+    wr = torch.zeros((R, tmotif.TM_WORK_FIELDS), dtype=torch.int64, device="cuda")
+    tmotif.tm_count(g.h, tr.h, roots=d_roots, per_root_work=wr, mode=tmotif.TM_SCHED_DYNAMIC, stats=True)
+    wb = wr.cpu().numpy()
+    yb = np.log1p(wb[:, 0] + wb[:, 2])
+    Xb = torch.zeros((R, tmotif.TM_FEATURES), dtype=torch.float32, device="cuda")
+    tmotif.tm_features(g.h, tr.h, d_roots, Xb)
+    pb = torch.zeros(R, dtype=torch.float32, device="cuda")
+    model.predict(Xb, pb)
+    p = pb.cpu().numpy()
+    rmse = float(np.sqrt(np.mean((p - yb) ** 2)))
+    rank_corr = float(np.corrcoef(np.argsort(np.argsort(p)), np.argsort(np.argsort(yb)))[0, 1]) if R > 2 else None
+    ro = torch.zeros_like(d_roots)
+    sp = torch.zeros_like(d_roots)
+    model.plan(Xb, d_roots, ro, sp, unit_work=args.unit_work, max_split=args.max_split)
+    out = {}
+    for name, m in (("planned", tmotif.TM_SCHED_PLANNED), ("planned_dynamic", tmotif.TM_SCHED_PLANNED | tmotif.TM_SCHED_DYNAMIC)):
+        mm = (mode & ~tmotif.TM_SCHED_DYNAMIC) | m
+        tmotif.tm_count(g.h, tr.h, mode=mm, roots=ro, counts=counts, root_split=sp, stream=stream)
+        torch.cuda.synchronize()
+        if not torch.equal(counts, ref_counts):
+            raise SystemExit("planned counts differ")
+        ts = []
+        for i in range(max(1, min(args.steps, 3))):
+            flush.fill_(i & 0xFF)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            tmotif.tm_count(g.h, tr.h, mode=mm, roots=ro, counts=counts, root_split=sp, stream=stream)
+            b.record(stream)
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b))
+        out[name + "_ms_per_step"] = statistics.median(ts)
+    out.update({"train_roots": n_train, "train_seconds": t_train, "final_train_loss": float(hist[-1]),
+                "label": "log1p(candidates + probes) per root", "rmse_log_work_on_bench_roots": rmse,
+                "spearman_on_bench_roots": rank_corr, "label_std_on_bench_roots": float(np.std(yb)),
+                "max_split": args.max_split, "unit_work": args.unit_work})
+    return out
+
+
+def run_batched(args):
+    """64 random motif sets merged into one tree (each motif with its set's
+    window), one persistent launch replayed from a CUDA graph, launch shape
+    and split thresholds from the autotuner."""
+    import torch
+    from paper_2507_14813_b300 import build, synth, tmotif
+    rank, local_rank, world = env_rank()
+    torch.cuda.set_device(local_rank)
+    build.build()
+    spec = synth.BATCHED_MILD
+    src, dst, t = synth.make_graph(spec)
+    sets = synth.batched_sets()
+    motifs, deltas = [], []
+    for ms, d in sets:
+        motifs += ms
+        deltas += [d] * len(ms)
+    g = tmotif.Graph(src, dst, t, spec.n_nodes, presorted=True)
+    tr = tmotif.Tree(motifs, deltas)
+    R = args.roots or 65536
+    roots = torch.from_numpy(synth.root_sample(100 + rank, len(src), R)).cuda()
+    D = tmotif.TM_SCHED_DYNAMIC
+    tune = tmotif.tm_autotune(g.h, tr.h, mode=D, roots=roots[:min(R, 8192)])
+    counts = torch.zeros(len(motifs), dtype=torch.int64, device="cuda")
+    ex = tmotif.Exec(g.h, tr.h, counts, mode=D, roots=roots, tune=tune)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        ex.launch(stream)
+    ex.status(stream)
+    ref = counts.clone()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    with ClockSampler(local_rank) as clk:
+        for i in range(args.steps):
+            flush.fill_(i & 0xFF)
+            ev[i][0].record(stream)
+            ex.launch(stream)
+            ev[i][1].record(stream)
+        torch.cuda.synchronize()
+    ex.status(stream)
+    if not torch.equal(counts, ref):
+        raise SystemExit("batched counts changed between replays")
+    ms = statistics.median([a.elapsed_time(b) for a, b in ev])
+    # the same sets launched one after another, each with its own tree
+    seq_ms = None
+    if not args.no_permotif:
+        trees = [tmotif.Tree(ms_, d) for ms_, d in sets]
+        outs = [torch.zeros(len(ms_), dtype=torch.int64, device="cuda") for ms_, _ in sets]
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for trx, o in zip(trees, outs):
+            tmotif.tm_count(g.h, trx.h, mode=D, roots=roots, counts=o, stream=stream)
+        b.record(stream)
+        torch.cuda.synchronize()
+        seq_ms = a.elapsed_time(b)
+        if not torch.equal(torch.cat(outs), ref):
+            raise SystemExit("per-set counts differ from the batched launch")
+    _, st = tmotif.tm_count(g.h, tr.h, mode=D, roots=roots, stats=True, tune=tune)
+    peak, peak_kind = measured_peaks()
+    achieved = st["algo_bytes"] / (ms / 1000.0) / 1e9
+    line = {
+        "metric": "query root-edges/sec (roots x motifs / s), 64 motif sets in one batched launch",
+        "value": R * len(motifs) / (ms / 1000.0), "unit": "root-edges/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+        "config": {"workload": "%s: %d nodes, %d edges, Zipf(%.1f), bursty; 64 random prefix-sharing sets "
+                               "(%d motifs of 2-6 edges, windows 600/3600/86400 s) merged into one tree; %d roots"
+                               % (spec.name, spec.n_nodes, spec.n_edges, spec.zipf_s, len(motifs), R),
+                   "l2": "flushed between steps (256 MiB write)", "launch": "CUDA graph replay of one persistent launch"},
+        "tree": tr.info(), "autotune": tune, "sets_one_by_one_ms": seq_ms,
+        "batched_speedup_vs_one_by_one": (seq_ms / ms) if seq_ms else None,
+        "work": {k: st[k] for k in ("candidates", "probes", "leaf_evals", "tasks_split", "algo_bytes")},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": None},
+        "gpu_launches": 3 * args.steps, "clocks": clk.summary(),
+    }
+    if rank == 0:
+        print(json.dumps(line))
+    return 0
+
+
+def run_serving(args):
+    """Poisson arrivals of motif queries against a resident graph; continuous
+    batching by the library's server; latency percentiles and throughput."""
+    import torch
+    from paper_2507_14813_b300 import build, synth, tmotif
+    rank, local_rank, world = env_rank()
+    torch.cuda.set_device(local_rank)
+    build.build()
+    spec = synth.SERVING_MILD if not args.serving_small else synth.BATCHED_MILD
+    t0 = time.perf_counter()
+    src, dst, t = synth.make_graph(spec)
+    t_gen = time.perf_counter() - t0
+    g = tmotif.Graph(src, dst, t, spec.n_nodes, presorted=True)
+    rate = args.rate
+    n_req = int(rate * args.duration)
+    rng = np.random.default_rng(7 + rank)
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, n_req))
+    qs = [synth.serving_query(50_000 + i, len(src), args.query_roots) for i in range(n_req)]
+    # warm-up requests
+    srv = tmotif.Server(g, streams=args.streams, max_batch=args.max_batch, mem_budget=args.mem_budget)
+    for i in range(4):
+        tk = srv.submit(*qs[i])
+        srv.poll(tk, wait=True)
+    tickets = []
+    start = time.perf_counter()
+    with ClockSampler(local_rank) as clk:
+        for i, q in enumerate(qs):
+            now = time.perf_counter() - start
+            if arrivals[i] > now:
+                time.sleep(arrivals[i] - now)
+            tickets.append(srv.submit(*q))
+        res = [srv.poll(tk, wait=True) for tk in tickets]
+        end = time.perf_counter()
+    info = srv.info()
+    srv.close()
+    lat = np.array([st["latency_ms"] for _, st in res])
+    sizes = np.array([st["batch_size"] for _, st in res])
+    # spot check: a few requests against tm_count alone
+    for i in range(0, n_req, max(1, n_req // 8)):
+        ms_, d, r = qs[i]
+        alone = tmotif.count(g, tmotif.Tree(ms_, d), roots=r, mode=tmotif.TM_SCHED_DYNAMIC)
+        if res[i][0].tolist() != alone.tolist():
+            raise SystemExit("served counts differ from the request counted alone")
+    wall = end - start
+    units = sum(len(q[0]) * len(q[2]) for q in qs)
+    line = {
+        "metric": "serving: p99 request latency (ms) under Poisson arrivals, continuous batching",
+        "value": float(np.percentile(lat, 99)), "unit": "ms", "n_gpus": world, "steps": n_req, "warmup": 4,
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+        "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+        "mean_ms": float(lat.mean()), "qps": n_req / wall, "root_edges_per_s": units / wall,
+        "mean_batch": float(sizes.mean()), "max_batch_seen": int(sizes.max()), "server": info,
+        "config": {"workload": "%s: %d nodes, %d edges, Zipf(%.1f), bursty; %d requests at %.0f/s (Poisson); "
+                               "each 1-16 motifs of 2-5 edges, window log-uniform in [60, 86400] s, %d sampled roots"
+                               % (spec.name, spec.n_nodes, spec.n_edges, spec.zipf_s, n_req, rate, args.query_roots),
+                   "streams": args.streams, "max_batch": args.max_batch, "mem_budget": args.mem_budget,
+                   "graph_generation_s": t_gen},
+        "clocks": clk.summary(),
+    }
+    if rank == 0:
+        print(json.dumps(line))
+    return 0
+
+
 def run_reference(args):
     rank, local_rank, world = env_rank()
     if rank != 0:
@@ -182,10 +387,25 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-permotif", action="store_true")
     ap.add_argument("--static", action="store_true", help="one warp per root, no subtree splitting")
+    ap.add_argument("--no-learned", action="store_true")
+    ap.add_argument("--train-roots", type=int, default=512)
+    ap.add_argument("--unit-work", type=float, default=2e6)
+    ap.add_argument("--max-split", type=int, default=512)
+    ap.add_argument("--rate", type=float, default=50.0)
+    ap.add_argument("--duration", type=float, default=20.0)
+    ap.add_argument("--query-roots", type=int, default=64)
+    ap.add_argument("--streams", type=int, default=2)
+    ap.add_argument("--max-batch", type=int, default=32)
+    ap.add_argument("--mem-budget", type=int, default=4 << 30)
+    ap.add_argument("--serving-small", action="store_true")
     ap.add_argument("--mode", type=int, default=0, help="extra tm_count mode bits")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batched":
+        return run_batched(args)
+    if args.workload == "serving":
+        return run_serving(args)
 
     import torch
     import torch.distributed as dist
@@ -260,6 +480,12 @@ def main():
             pm.append(a.elapsed_time(b))
         perm = statistics.median(pm)
 
+    # learned scheduling: a cost model trained on measured work of a separate
+    # root sample orders the benchmark's roots and cuts the heavy ones
+    learned = None
+    if not args.no_learned:
+        learned = learned_schedule(args, tmotif, g, tr, src, rank, d_roots, counts, ref_counts, stream, flush, mode)
+
     # end to end through the C-ABI with host buffers: load, build, count, read back
     e2e = None
     if not args.no_e2e:
@@ -300,6 +526,8 @@ def main():
         "gpu_launches": 2 * args.steps,
         "clocks": clk.summary(),
     }
+    if learned:
+        line["learned_schedule"] = learned
     if e2e:
         line["e2e"] = e2e
     if rank == 0 and not args.no_cpu_baseline:

@@ -161,6 +161,10 @@ typedef struct {
     int32_t ctas_per_sm;      /* 0: library default */
     int32_t reserved;
     const int32_t *root_split; /* device, per root: slices for TM_SCHED_PLANNED (<= 1: none), or NULL */
+    int32_t poll_every;       /* TM_SCHED_DYNAMIC: chunk loads between looks for idle warps (0: default 4) */
+    int32_t donate_seq;       /* min unscanned entries to split a level that descends (0: default 64) */
+    int32_t donate_leaf;      /* ... a level whose survivors are only counted (0: default 1024) */
+    int32_t reserved2;
 } tm_count_args;
 
 typedef struct {
@@ -193,6 +197,92 @@ typedef struct {
  */
 int tm_count(const tm_graph *g, const tm_tree *tr, const tm_count_args *args, int64_t *counts,
              tm_run_stats *stats, void *stream);
+
+/* ------------------------------------------------------------ serving */
+/*
+ * A request loop over a resident graph with continuous batching.  The paper
+ * answers one query per run (Section 4.1); serving is an addition of this
+ * library.  A worker thread keeps up to `streams` batches on the device.
+ * When a stream is free it admits the oldest pending requests (at most
+ * `max_batch` <= 64, within `mem_budget` device bytes), merges their motifs
+ * into one MG-Tree (each motif keeps its own window and its request), runs
+ * one count over the union of their roots (each root counted only for the
+ * requests that listed it) and scatters the counts back.  Requests that
+ * arrive while batches run are admitted as streams and memory free up, so
+ * their work overlaps on the device.  Each request gets exactly the counts
+ * that tm_count gives for its motifs, windows and roots alone.
+ */
+typedef struct tm_server tm_server;
+
+typedef struct {
+    int32_t streams;          /* batches in flight (default 2, at most 16) */
+    int32_t max_batch;        /* requests merged into one batch (default 32, at most 64) */
+    int64_t mem_budget;       /* device bytes for admitted batches (default 4 GiB); a
+                                 request that alone exceeds it fails with TM_ENOMEM */
+    uint32_t mode;            /* count mode of every batch: 0, TM_SCHED_DYNAMIC (default
+                                 when cfg is NULL), | TM_LEAF_SCAN */
+    uint32_t reserved;
+} tm_server_config;
+
+typedef struct {
+    double queue_ms;          /* submit -> batch launch */
+    double latency_ms;        /* submit -> counts ready on the host */
+    int32_t batch;            /* batch id */
+    int32_t batch_size;       /* requests in that batch */
+} tm_request_stats;
+
+typedef struct {
+    int64_t batches;
+    int64_t requests_done;
+    int64_t pending;
+    int64_t in_flight;        /* batches on the device */
+    int64_t admitted_bytes;   /* bytes counted against the budget now */
+    int64_t peak_admitted_bytes;
+} tm_server_info;
+
+/* The graph must outlive the server.  cfg may be NULL for the defaults. */
+int tm_server_open(const tm_graph *g, const tm_server_config *cfg, tm_server **out);
+/* Copy a request (motifs as for tm_tree_build, host root list) into the
+ * queue; *ticket identifies it.  Motifs are validated here (TM_EINVAL /
+ * TM_EUNSUPPORTED as tm_tree_build); a root outside [0, n_edges) is TM_EINVAL. */
+int tm_server_submit(tm_server *s, const int8_t *motif_uv, const int32_t *motif_off, int32_t n_motifs,
+                     const int64_t *delta, const int32_t *roots, int64_t n_roots, int64_t *ticket);
+/* 1 when done (counts, n_motifs int64, and stats filled; the ticket is then
+ * released), 0 while pending (wait = 0), or the request's error code.  With
+ * wait != 0 the call blocks until the request finishes. */
+int tm_server_poll(tm_server *s, int64_t ticket, int32_t wait, int64_t *counts, tm_request_stats *stats);
+int tm_server_get_info(tm_server *s, tm_server_info *info);
+/* Finishes every admitted and pending request, then stops the worker. */
+int tm_server_close(tm_server *s);
+
+/* ------------------------------------------------------------ replay and tuning */
+/*
+ * A count captured once as a CUDA graph and replayed: scratch is allocated
+ * at creation, each replay resets it, runs the mining launches and writes
+ * the counts to `counts` (device, n_motifs int64).  `args` must name device
+ * roots (TM_ROOTS_DEVICE) or a range; per-root outputs and stats are not
+ * available.  Used for batches of many motif sets (one tree built from all
+ * of them, each motif with its own window) launched repeatedly.
+ * tm_exec_status synchronises `stream` and returns TM_ETIMEOUT when a bounded
+ * device wait expired in the last replay.
+ */
+typedef struct tm_exec tm_exec;
+int tm_exec_create(const tm_graph *g, const tm_tree *tr, const tm_count_args *args, int64_t *counts, void *stream,
+                   tm_exec **out);
+int tm_exec_launch(tm_exec *x, void *stream);
+int tm_exec_status(tm_exec *x, void *stream);
+int tm_exec_free(tm_exec *x);
+
+/* Launch shape and split thresholds picked by tm_autotune (times a grid on the
+ * caller's roots, best of two runs each; the counts are not returned). */
+typedef struct {
+    int32_t ctas_per_sm;
+    int32_t donate_seq;
+    int32_t donate_leaf;
+    int32_t poll_every;
+    float ms;                 /* time of the chosen configuration */
+} tm_tune;
+int tm_autotune(const tm_graph *g, const tm_tree *tr, const tm_count_args *args, tm_tune *best, void *stream);
 
 /*
  * Allocation-free counting.  The paper has no counterpart: this is a

@@ -84,6 +84,7 @@ static constexpr uint8_t kNodeStarLeaf = 2;  // ... and that last edge extends t
 static constexpr uint8_t kNodeStarKids = 4;  // some single-edge leaf child has kNodeStarLeaf
 
 struct DevNode {
+    uint64_t qmask;          // queries (bit q) with a ref in this node's subtree
     int8_t k_begin;          // first level owned by this node (= |C_parent|)
     int8_t k_end;            // |C_N|
     int8_t flags;
@@ -102,7 +103,8 @@ struct DevNode {
 
 struct DevRef {
     int32_t counter;         // index into the caller's motif list
-    int32_t delta;           // index into the window table
+    int16_t delta;           // index into the window table
+    int16_t query;           // query the motif belongs to (0..63; 0 outside serving batches)
 };
 
 struct DevTree {
@@ -126,6 +128,7 @@ struct HostNode {
 struct HostTree {
     std::vector<HostNode> nodes;
     std::vector<int64_t> motif_delta;          // window of each caller motif
+    std::vector<int32_t> motif_query;          // query of each caller motif (empty: all 0)
     int32_t n_motifs = 0;
     int32_t n_leaves = 0;
     int32_t depth = 0;
@@ -173,6 +176,9 @@ void graph_release(tm_graph *g);
 
 // tree build (tm_tree.cpp)
 int tree_build(const int8_t *uv, const int32_t *off, int32_t n, const int64_t *delta, tm_tree **out);
+// the same, with the query (0..63) of every motif for masked counting
+int tree_build_q(const int8_t *uv, const int32_t *off, int32_t n, const int64_t *delta, const int32_t *query,
+                 tm_tree **out);
 void tree_release(tm_tree *tr);
 // device copy of tree `which` (0 = MG-Tree, 1 + i = chain i), uploaded on first use
 int tree_device(const tm_tree *tr, int which, bool par_leaves, cudaStream_t s, DevTree *out);
@@ -180,5 +186,11 @@ int tree_device(const tm_tree *tr, int which, bool par_leaves, cudaStream_t s, D
 // mining (tm_mine.cu)
 int mine(const tm_graph *g, const tm_tree *tr, const tm_count_args *args, int64_t *counts,
          tm_run_stats *stats, cudaStream_t s);
+// a serving batch: MG-Tree already on the device (dt), roots with query masks;
+// no allocation, no synchronisation
+size_t batch_scratch_bytes(const tm_graph *g, const tm_tree *tr, uint32_t mode);
+int batch_enqueue(const tm_graph *g, const tm_tree *tr, uint32_t mode, const DevTree &dt, const int32_t *d_roots,
+                  const uint64_t *d_qmask, int64_t n_roots, char *scratch, int64_t *d_counts, int32_t *d_status,
+                  cudaStream_t s);
 
 }  // namespace tmo

@@ -49,9 +49,9 @@ constexpr int kSmemCounters = 2048;       // per-CTA counters kept in shared mem
 constexpr int kLaneScanMax = 24;          // leaf windows up to this size are scanned by the lane
 
 constexpr int kQueueCap = 1 << 20;        // tasks per launch (slots are not reused)
-constexpr int kPollEvery = 4;             // chunk loads between looks at the idle counter
-constexpr int kDonateSeq = 64;            // min unscanned entries to split a level that descends
-constexpr int kDonateLeaf = 1024;         // ... a level whose survivors are only counted
+constexpr int kPollEvery = 4;             // default: chunk loads between looks at the idle counter
+constexpr int kDonateSeq = 64;            // default: min unscanned entries to split a level that descends
+constexpr int kDonateLeaf = 1024;         // default: ... a level whose survivors are only counted
 constexpr long long kReadySpins = 1 << 22;  // bound on waiting for a claimed task's payload
 constexpr long long kIdleSpins = 1 << 20;   // bound on an idle warp's wait for work
 
@@ -98,6 +98,11 @@ struct Params {
     int32_t dynamic;                  // 1: persistent launch with a task queue
     int32_t react;                    // 1: warps donate slices when others are idle
     const int32_t *split;             // per root index: slices for its first-level lists, or null
+    int32_t poll_every;               // chunk loads between looks at the idle counter
+    int32_t donate_seq;               // min unscanned entries to split a level that descends
+    int32_t donate_leaf;              // ... a level whose survivors are only counted
+    int32_t pad2;
+    const uint64_t *root_qmask;       // per root index: queries it serves (bit q), or null = all
 };
 
 enum { kStCand = 0, kStExp, kStListProbe, kStHashProbe, kStPairProbe, kStLeaf, kStRoots, kStSplit, kStatFields };
@@ -262,9 +267,10 @@ struct Miner {
     int64_t ri;                        // root index of the current work (per-root outputs)
     int polls;                         // chunk loads since the last look at the idle counter
     int split_h;                       // planned slices for the current root's first-level lists
+    uint64_t rmask;                    // queries served by the current root
 
     __device__ Miner(const Params &pp, WarpState &s, unsigned long long *c, int l)
-        : p(pp), ws(s), s_cnt(c), lane(l), polls(0), split_h(0) {
+        : p(pp), ws(s), s_cnt(c), lane(l), polls(0), split_h(0), rmask(~0ull) {
         for (int i = 0; i < kStatFields; i++) w.v[i] = 0;
     }
 
@@ -347,6 +353,7 @@ struct Miner {
         const uint32_t le = (lane == 31) ? 0xffffffffu : ((2u << lane) - 1u);   // lanes <= this one
         for (int i = 0; i < L.n_ref; i++) {
             const DevRef ref = p.tr.refs[L.ref_begin + i];
+            if (!((rmask >> ref.query) & 1ull)) continue;
             const int32_t hi = ws.ehi[ref.delta];
             unsigned long long c = 0;
             if (((S >> lane) & 1u) && last < hi) {
@@ -387,6 +394,7 @@ struct Miner {
         if (complete && N.n_ref > 0) {                     // Q_N counted (Algorithm 3)
             for (int i = 0; i < N.n_ref; i++) {
                 const DevRef ref = p.tr.refs[N.ref_begin + i];
+                if (!((rmask >> ref.query) & 1ull)) continue;
                 uint32_t in = __ballot_sync(0xffffffffu, c.y <= ws.ehi[ref.delta]) & S;
                 if (lane == 0) add_count(ref.counter, (unsigned long long)__popc(in));
             }
@@ -394,6 +402,7 @@ struct Miner {
         if (complete && N.n_par > 0) {
             for (int ci = 0; ci < N.n_par; ci++) {
                 const DevNode L = p.tr.nodes[N.child_begin + N.n_seq + ci];
+                if (!(L.qmask & rmask)) continue;
                 uint32_t S2 = __ballot_sync(0xffffffffu, c.y < ws.ehi[L.dmax]) & S;
                 if (S2) leaf_batch(L, k, S2, uk, vk, cs, cd, c.y, N.dmax, suf);
             }
@@ -479,6 +488,10 @@ struct Miner {
     // its list with edge ids in (eid[k-1], ehi].
     __device__ void open(int k, int node, int sib_end) {
         const DevNode N = p.tr.nodes[node];
+        if (!(N.qmask & rmask)) {                       // no query of this root below this node
+            set_frame(k, node, sib_end, kListGlobal, 0, 0, 0, false, 0, false, 0);
+            return;
+        }
         const int32_t last = ws.eid[k - 1];
         const int32_t hi = ws.ehi[N.dmax];
         int8_t lt;
@@ -563,7 +576,7 @@ struct Miner {
         for (int kb = max(kbase, 1); kb <= top; kb++) {
             const int64_t pos = ws.pos[kb], end = ws.end[kb];
             const int64_t rem = end - pos;
-            if (rem < (ws.seq[kb] ? kDonateSeq : kDonateLeaf)) continue;
+            if (rem < (ws.seq[kb] ? p.donate_seq : p.donate_leaf)) continue;
             const int64_t mid = pos + (((rem >> 1) + 31) & ~31ll);
             if (push_task(kb, mid, end)) {
                 __syncwarp();
@@ -739,7 +752,7 @@ struct Miner {
                 continue;
             }
             if (ws.pos[k] < ws.end[k]) {
-                if (p.react && ++polls >= kPollEvery) {
+                if (p.react && ++polls >= p.poll_every) {
                     polls = 0;
                     maybe_donate(kbase, k);
                 }
@@ -829,6 +842,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_mine(Params p) {
             if (M.pop(tk)) {
                 M.ri = tk.ri;
                 M.split_h = 0;
+                M.rmask = p.root_qmask ? __ldg(p.root_qmask + tk.ri) : ~0ull;
                 Work before = M.w;
                 M.task(tk);
                 flush_work(M, before, p, lane);
@@ -843,6 +857,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_mine(Params p) {
             for (int64_t ri = (int64_t)first; ri < last; ri++) {
                 M.ri = ri;
                 M.split_h = p.split ? __ldg(p.split + ri) : 0;
+                M.rmask = p.root_qmask ? __ldg(p.root_qmask + ri) : ~0ull;
                 const int32_t r = p.roots ? __ldg(p.roots + ri) : (int32_t)(p.root_lo + ri);
                 Work before = M.w;
                 M.root(r);
@@ -872,31 +887,151 @@ __global__ void k_to_i64(const unsigned long long *a, int64_t *b, int n) {
 
 }  // namespace
 
-int mine(const tm_graph *g, const tm_tree *tr, const tm_count_args *args, int64_t *counts,
-         tm_run_stats *stats, cudaStream_t s) {
-    const int n_motifs = tr->h.n_motifs;
-    const bool comine = (args->mode & TM_PERMOTIF) == 0;
-    const bool par = (args->mode & TM_LEAF_SCAN) == 0;
-    const bool react = (args->mode & TM_SCHED_DYNAMIC) != 0;
-    const bool planned = (args->mode & TM_SCHED_PLANNED) != 0;
-    const bool dynamic = react || planned;
-    if (planned && !args->root_split) {
+namespace {
+
+__global__ void k_status(const QueueHdr *q, int n_launch, int32_t *status) {
+    int e = 0;
+    for (int i = 0; i < n_launch; i++) e |= q[i].error;
+    *status = e;
+}
+
+// Everything a count needs besides its inputs: where the scratch lives and
+// how the launches are shaped.
+struct Plan {
+    int n_motifs = 0, n_launch = 0;
+    bool comine = true, par = true, react = false, planned = false, dynamic = false, stats = false;
+    int64_t n_roots = 0, root_lo = 0;
+    const int32_t *roots = nullptr;     // device
+    const uint64_t *root_qmask = nullptr; // device, serving batches only
+    int blocks = 0, dyn_smem = 0;
+    bool smem_cnt = true;
+    int32_t chunk = 1;
+    int poll_every = kPollEvery, donate_seq = kDonateSeq, donate_leaf = kDonateLeaf;
+    size_t o_q = 0, o_tasks = 0, o_ready = 0, bytes = 0, b_ready = 0;
+};
+
+int make_plan(const tm_graph *g, const tm_tree *tr, const tm_count_args *args, bool stats, Plan *P) {
+    P->n_motifs = tr->h.n_motifs;
+    P->comine = (args->mode & TM_PERMOTIF) == 0;
+    P->par = (args->mode & TM_LEAF_SCAN) == 0;
+    P->react = (args->mode & TM_SCHED_DYNAMIC) != 0;
+    P->planned = (args->mode & TM_SCHED_PLANNED) != 0;
+    P->dynamic = P->react || P->planned;
+    P->stats = stats;
+    if (P->planned && !args->root_split) {
         set_error("tm_count: TM_SCHED_PLANNED needs root_split");
         return TM_EINVAL;
     }
-    const bool want_stats = stats != nullptr;
-    int64_t n_roots;
     if (args->roots) {
-        n_roots = args->n_roots;
+        P->n_roots = args->n_roots;
+        P->root_lo = 0;
     } else {
         int64_t hi = args->root_hi > 0 ? args->root_hi : g->d.E;
         if (args->root_lo < 0 || hi > g->d.E || args->root_lo > hi) {
             set_error("tm_count: root range outside [0, n_edges]");
             return TM_EINVAL;
         }
-        n_roots = hi - args->root_lo;
+        P->n_roots = hi - args->root_lo;
+        P->root_lo = args->root_lo;
     }
-    if (n_roots < 0) { set_error("tm_count: n_roots < 0"); return TM_EINVAL; }
+    if (P->n_roots < 0) { set_error("tm_count: n_roots < 0"); return TM_EINVAL; }
+    if (args->poll_every > 0) P->poll_every = args->poll_every;
+    if (args->donate_seq > 0) P->donate_seq = args->donate_seq;
+    if (args->donate_leaf > 0) P->donate_leaf = args->donate_leaf;
+    P->n_launch = P->comine ? 1 : (int)tr->chains.size();
+    const size_t b_cnt = sizeof(unsigned long long) * (size_t)(P->n_motifs + kStatFields);
+    P->o_q = (b_cnt + 255) / 256 * 256;
+    const size_t b_q = sizeof(QueueHdr) * (size_t)P->n_launch;
+    P->o_tasks = (P->o_q + b_q + 255) / 256 * 256;
+    const size_t b_tasks = P->dynamic ? sizeof(Task) * kQueueCap : 0;
+    P->o_ready = P->o_tasks + b_tasks;
+    P->b_ready = P->dynamic ? sizeof(int) * kQueueCap : 0;
+    P->bytes = P->o_ready + P->b_ready;
+
+    int dev = 0, n_sm = 0;
+    TM_CUDA_TRY(cudaGetDevice(&dev));
+    TM_CUDA_TRY(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev));
+    P->smem_cnt = P->n_motifs <= kSmemCounters;
+    P->dyn_smem = P->smem_cnt ? (int)(sizeof(unsigned long long) * P->n_motifs) : 0;
+    int per_sm = 0;
+    TM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, stats ? k_mine<true> : k_mine<false>,
+                                                              kThreads, P->dyn_smem));
+    if (args->ctas_per_sm > 0) per_sm = std::min(per_sm, (int)args->ctas_per_sm);
+    per_sm = std::max(per_sm, 1);
+    P->blocks = n_sm * per_sm;
+    const int64_t warps_total = (int64_t)P->blocks * kWarps;
+    P->chunk = (int32_t)std::max<int64_t>(1, std::min<int64_t>(16, P->n_roots / (warps_total * 64)));
+    return TM_OK;
+}
+
+// Enqueue a count on `s`: scratch reset, mining launches, counts (int64) to
+// `counts_dev` when non-null, error bits to `status_dev` when non-null.  No
+// allocation and no synchronisation, so it can be captured in a CUDA graph
+// (the tree must already be on the device).
+int enqueue(const tm_graph *g, const tm_tree *tr, const tm_count_args *args, const Plan &P, char *scratch,
+            int64_t *counts_dev, int32_t *status_dev, cudaStream_t s, int64_t *launches,
+            const DevTree *given = nullptr) {
+    unsigned long long *d_cnt = (unsigned long long *)scratch;
+    unsigned long long *d_st = d_cnt + P.n_motifs;
+    QueueHdr *d_q = (QueueHdr *)(scratch + P.o_q);
+    Task *d_tasks = P.dynamic ? (Task *)(scratch + P.o_tasks) : nullptr;
+    int *d_ready = P.dynamic ? (int *)(scratch + P.o_ready) : nullptr;
+    TM_CUDA_TRY(cudaMemsetAsync(scratch, 0, P.o_tasks, s));
+    if (args->per_root_counts && P.n_roots > 0)
+        TM_CUDA_TRY(cudaMemsetAsync(args->per_root_counts, 0, sizeof(int64_t) * P.n_roots * P.n_motifs, s));
+    if (args->per_root_work && P.n_roots > 0)
+        TM_CUDA_TRY(cudaMemsetAsync(args->per_root_work, 0, sizeof(int64_t) * P.n_roots * TM_WORK_FIELDS, s));
+    auto kern = P.stats ? k_mine<true> : k_mine<false>;
+    int64_t n = 0;
+    for (int L = 0; L < P.n_launch && P.n_roots > 0; L++) {
+        DevTree dt;
+        if (given) dt = *given;
+        else TM_TRY(tree_device(tr, P.comine ? 0 : 1 + L, P.par, s, &dt));
+        if (P.dynamic) TM_CUDA_TRY(cudaMemsetAsync(d_ready, 0, P.b_ready, s));
+        Params prm;
+        prm.g = g->d;
+        prm.tr = dt;
+        prm.roots = P.roots;
+        prm.n_roots = P.n_roots;
+        prm.root_lo = P.root_lo;
+        prm.counts = d_cnt;
+        prm.per_root_counts = args->per_root_counts;
+        prm.per_root_work = args->per_root_work;
+        prm.q = d_q + L;
+        prm.tasks = d_tasks;
+        prm.ready = d_ready;
+        prm.stats = d_st;
+        prm.chunk = P.chunk;
+        prm.smem_counters = P.smem_cnt ? 1 : 0;
+        prm.dynamic = P.dynamic ? 1 : 0;
+        prm.react = P.react ? 1 : 0;
+        prm.split = P.planned ? args->root_split : nullptr;
+        prm.poll_every = P.poll_every;
+        prm.donate_seq = P.donate_seq;
+        prm.donate_leaf = P.donate_leaf;
+        prm.pad2 = 0;
+        prm.root_qmask = P.root_qmask;
+        kern<<<P.blocks, kThreads, P.dyn_smem, s>>>(prm);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) {
+            set_error(std::string("tm_count: launch: ") + cudaGetErrorString(e));
+            return TM_ECUDA;
+        }
+        n++;
+    }
+    if (counts_dev) {
+        k_to_i64<<<(P.n_motifs + 255) / 256, 256, 0, s>>>(d_cnt, counts_dev, P.n_motifs);
+        TM_CUDA_TRY(cudaGetLastError());
+    }
+    if (status_dev) {
+        k_status<<<1, 1, 0, s>>>(d_q, P.n_launch, status_dev);
+        TM_CUDA_TRY(cudaGetLastError());
+    }
+    if (launches) *launches = n;
+    return TM_OK;
+}
+
+int check_roots(const tm_graph *g, const tm_count_args *args, int64_t n_roots) {
     if (args->roots && !(args->flags & TM_ROOTS_DEVICE)) {
         for (int64_t i = 0; i < n_roots; i++)
             if (args->roots[i] < 0 || args->roots[i] >= g->d.E) {
@@ -904,24 +1039,45 @@ int mine(const tm_graph *g, const tm_tree *tr, const tm_count_args *args, int64_
                 return TM_EINVAL;
             }
     }
+    return TM_OK;
+}
 
-    // device scratch: counters, stats, one queue header per launch, task queue
-    const int n_launch = comine ? 1 : (int)tr->chains.size();
-    const size_t b_cnt = sizeof(unsigned long long) * (size_t)(n_motifs + kStatFields);
-    const size_t o_q = (b_cnt + 255) / 256 * 256;
-    const size_t b_q = sizeof(QueueHdr) * (size_t)n_launch;
-    const size_t o_tasks = (o_q + b_q + 255) / 256 * 256;
-    const size_t b_tasks = dynamic ? sizeof(Task) * kQueueCap : 0;
-    const size_t o_ready = o_tasks + b_tasks;
-    const size_t b_ready = dynamic ? sizeof(int) * kQueueCap : 0;
-    const size_t bytes = o_ready + b_ready;
+}  // namespace
+
+size_t batch_scratch_bytes(const tm_graph *g, const tm_tree *tr, uint32_t mode) {
+    tm_count_args a;
+    memset(&a, 0, sizeof(a));
+    a.mode = mode & ~(uint32_t)(TM_PERMOTIF | TM_SCHED_PLANNED);
+    a.root_lo = 0;
+    a.root_hi = 0;
+    Plan P;
+    if (make_plan(g, tr, &a, false, &P) != TM_OK) return 0;
+    return P.bytes;
+}
+
+int batch_enqueue(const tm_graph *g, const tm_tree *tr, uint32_t mode, const DevTree &dt, const int32_t *d_roots,
+                  const uint64_t *d_qmask, int64_t n_roots, char *scratch, int64_t *d_counts, int32_t *d_status,
+                  cudaStream_t s) {
+    tm_count_args a;
+    memset(&a, 0, sizeof(a));
+    a.mode = mode & ~(uint32_t)(TM_PERMOTIF | TM_SCHED_PLANNED);
+    a.flags = TM_ROOTS_DEVICE;
+    a.roots = d_roots;
+    a.n_roots = n_roots;
+    Plan P;
+    TM_TRY(make_plan(g, tr, &a, false, &P));
+    P.roots = d_roots;
+    P.root_qmask = d_qmask;
+    return enqueue(g, tr, &a, P, scratch, d_counts, d_status, s, nullptr, &dt);
+}
+
+int mine(const tm_graph *g, const tm_tree *tr, const tm_count_args *args, int64_t *counts,
+         tm_run_stats *stats, cudaStream_t s) {
+    Plan P;
+    TM_TRY(make_plan(g, tr, args, stats != nullptr, &P));
+    TM_TRY(check_roots(g, args, P.n_roots));
     char *scratch = nullptr;
-    TM_CUDA_TRY(cudaMallocAsync((void **)&scratch, bytes, s));
-    unsigned long long *d_cnt = (unsigned long long *)scratch;
-    unsigned long long *d_st = d_cnt + n_motifs;
-    QueueHdr *d_q = (QueueHdr *)(scratch + o_q);
-    Task *d_tasks = dynamic ? (Task *)(scratch + o_tasks) : nullptr;
-    int *d_ready = dynamic ? (int *)(scratch + o_ready) : nullptr;
+    TM_CUDA_TRY(cudaMallocAsync((void **)&scratch, P.bytes, s));
     void *roots_copy = nullptr;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     auto finish = [&](int code) {
@@ -931,81 +1087,30 @@ int mine(const tm_graph *g, const tm_tree *tr, const tm_count_args *args, int64_
         cudaFreeAsync(scratch, s);
         return code;
     };
-    // ready flags only need zeroing between launches; counters and headers once
-    if (cudaMemsetAsync(scratch, 0, o_tasks, s) != cudaSuccess) { set_error("tm_count: memset"); return finish(TM_ECUDA); }
-
-    const int32_t *d_roots = args->roots;
-    if (args->roots && !(args->flags & TM_ROOTS_DEVICE) && n_roots > 0) {
-        if (cudaMallocAsync(&roots_copy, sizeof(int32_t) * n_roots, s) != cudaSuccess) {
+    P.roots = args->roots;
+    if (args->roots && !(args->flags & TM_ROOTS_DEVICE) && P.n_roots > 0) {
+        if (cudaMallocAsync(&roots_copy, sizeof(int32_t) * P.n_roots, s) != cudaSuccess) {
             set_error("tm_count: root list allocation");
             return finish(TM_ENOMEM);
         }
-        cudaMemcpyAsync(roots_copy, args->roots, sizeof(int32_t) * n_roots, cudaMemcpyHostToDevice, s);
-        d_roots = (const int32_t *)roots_copy;
+        cudaMemcpyAsync(roots_copy, args->roots, sizeof(int32_t) * P.n_roots, cudaMemcpyHostToDevice, s);
+        P.roots = (const int32_t *)roots_copy;
     }
-    if (args->per_root_counts && n_roots > 0)
-        cudaMemsetAsync(args->per_root_counts, 0, sizeof(int64_t) * n_roots * n_motifs, s);
-    if (args->per_root_work && n_roots > 0)
-        cudaMemsetAsync(args->per_root_work, 0, sizeof(int64_t) * n_roots * TM_WORK_FIELDS, s);
-
-    int dev = 0, n_sm = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
-    const bool smem_cnt = n_motifs <= kSmemCounters;
-    const int dyn_smem = smem_cnt ? (int)(sizeof(unsigned long long) * n_motifs) : 0;
-    auto kern = want_stats ? k_mine<true> : k_mine<false>;
-    int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, dyn_smem);
-    if (args->ctas_per_sm > 0) per_sm = std::min(per_sm, (int)args->ctas_per_sm);
-    per_sm = std::max(per_sm, 1);
-    const int blocks = n_sm * per_sm;
-    const int64_t warps_total = (int64_t)blocks * kWarps;
-    int32_t chunk = (int32_t)std::max<int64_t>(1, std::min<int64_t>(16, n_roots / (warps_total * 64)));
-
-    if (want_stats) {
+    const bool dev_counts = (args->flags & TM_COUNTS_DEVICE) != 0;
+    if (stats) {
         cudaEventCreate(&e0);
         cudaEventCreate(&e1);
         cudaEventRecord(e0, s);
     }
     int64_t launches = 0;
-    for (int L = 0; L < n_launch && n_roots > 0; L++) {
-        DevTree dt;
-        int rc = tree_device(tr, comine ? 0 : 1 + L, par, s, &dt);
-        if (rc != TM_OK) return finish(rc);
-        if (dynamic && L > 0) cudaMemsetAsync(d_ready, 0, b_ready, s);
-        Params prm;
-        prm.g = g->d;
-        prm.tr = dt;
-        prm.roots = d_roots;
-        prm.n_roots = n_roots;
-        prm.root_lo = args->roots ? 0 : args->root_lo;
-        prm.counts = d_cnt;
-        prm.per_root_counts = args->per_root_counts;
-        prm.per_root_work = args->per_root_work;
-        prm.q = d_q + L;
-        prm.tasks = d_tasks;
-        prm.ready = d_ready;
-        prm.stats = d_st;
-        prm.chunk = chunk;
-        prm.smem_counters = smem_cnt ? 1 : 0;
-        prm.dynamic = dynamic ? 1 : 0;
-        prm.react = react ? 1 : 0;
-        prm.split = planned ? args->root_split : nullptr;
-        if (dynamic && L == 0) cudaMemsetAsync(d_ready, 0, b_ready, s);
-        kern<<<blocks, kThreads, dyn_smem, s>>>(prm);
-        cudaError_t e = cudaGetLastError();
-        if (e != cudaSuccess) {
-            set_error(std::string("tm_count: launch: ") + cudaGetErrorString(e));
-            return finish(TM_ECUDA);
-        }
-        launches++;
-    }
-    if (want_stats) cudaEventRecord(e1, s);
+    int rc = enqueue(g, tr, args, P, scratch, nullptr, nullptr, s, &launches);
+    if (rc != TM_OK) return finish(rc);
+    if (stats) cudaEventRecord(e1, s);
 
     // the dynamic mode reports expired waits; that needs the queue headers back
-    if (dynamic) {
-        std::vector<QueueHdr> hq(n_launch);
-        cudaMemcpyAsync(hq.data(), d_q, sizeof(QueueHdr) * n_launch, cudaMemcpyDeviceToHost, s);
+    if (P.dynamic) {
+        std::vector<QueueHdr> hq(P.n_launch);
+        cudaMemcpyAsync(hq.data(), scratch + P.o_q, sizeof(QueueHdr) * P.n_launch, cudaMemcpyDeviceToHost, s);
         cudaError_t e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) {
             set_error(std::string("tm_count: ") + cudaGetErrorString(e));
@@ -1017,21 +1122,22 @@ int mine(const tm_graph *g, const tm_tree *tr, const tm_count_args *args, int64_
                 return finish(TM_ETIMEOUT);
             }
     }
-    if (args->flags & TM_COUNTS_DEVICE) {
-        k_to_i64<<<(n_motifs + 255) / 256, 256, 0, s>>>(d_cnt, counts, n_motifs);
+    const unsigned long long *d_cnt = (const unsigned long long *)scratch;
+    if (dev_counts) {
+        k_to_i64<<<(P.n_motifs + 255) / 256, 256, 0, s>>>(d_cnt, counts, P.n_motifs);
     } else {
-        std::vector<unsigned long long> h(n_motifs);
-        cudaMemcpyAsync(h.data(), d_cnt, sizeof(unsigned long long) * n_motifs, cudaMemcpyDeviceToHost, s);
+        std::vector<unsigned long long> h(P.n_motifs);
+        cudaMemcpyAsync(h.data(), d_cnt, sizeof(unsigned long long) * P.n_motifs, cudaMemcpyDeviceToHost, s);
         cudaError_t e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) {
             set_error(std::string("tm_count: ") + cudaGetErrorString(e));
             return finish(TM_ECUDA);
         }
-        for (int i = 0; i < n_motifs; i++) counts[i] = (int64_t)h[i];
+        for (int i = 0; i < P.n_motifs; i++) counts[i] = (int64_t)h[i];
     }
-    if (want_stats) {
+    if (stats) {
         unsigned long long hs[kStatFields];
-        cudaMemcpyAsync(hs, d_st, sizeof(hs), cudaMemcpyDeviceToHost, s);
+        cudaMemcpyAsync(hs, d_cnt + P.n_motifs, sizeof(hs), cudaMemcpyDeviceToHost, s);
         cudaError_t e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) {
             set_error(std::string("tm_count: ") + cudaGetErrorString(e));
@@ -1055,6 +1161,160 @@ int mine(const tm_graph *g, const tm_tree *tr, const tm_count_args *args, int64_
 }
 
 }  // namespace tmo
+
+// ---------------------------------------------------------------------------
+// Replayable counts: one tm_count configuration captured once in a CUDA graph.
+
+struct tm_exec {
+    cudaGraphExec_t exec = nullptr;
+    char *scratch = nullptr;
+    int32_t *status = nullptr;     // device, error bits of the last replay
+};
+
+extern "C" int tm_exec_create(const tm_graph *g, const tm_tree *tr, const tm_count_args *args, int64_t *counts,
+                              void *stream, tm_exec **out) {
+    using namespace tmo;
+    if (!g || !tr || !args || !counts || !out) { set_error("tm_exec_create: NULL argument"); return TM_EINVAL; }
+    *out = nullptr;
+    if (args->roots && !(args->flags & TM_ROOTS_DEVICE)) {
+        set_error("tm_exec_create: roots must be device memory (TM_ROOTS_DEVICE)");
+        return TM_EINVAL;
+    }
+    Plan P;
+    TM_TRY(make_plan(g, tr, args, false, &P));
+    P.roots = args->roots;
+    cudaStream_t s = (cudaStream_t)stream;
+    // trees go to the device before capture
+    for (int L = 0; L < P.n_launch; L++) {
+        DevTree dt;
+        TM_TRY(tree_device(tr, P.comine ? 0 : 1 + L, P.par, s, &dt));
+    }
+    tm_exec *x = new tm_exec();
+    auto fail = [&](int code) {
+        if (x->exec) cudaGraphExecDestroy(x->exec);
+        if (x->scratch) cudaFree(x->scratch);
+        if (x->status) cudaFree(x->status);
+        delete x;
+        return code;
+    };
+    if (cudaMalloc((void **)&x->scratch, P.bytes) != cudaSuccess || cudaMalloc((void **)&x->status, 4) != cudaSuccess) {
+        set_error("tm_exec_create: scratch allocation");
+        return fail(TM_ENOMEM);
+    }
+    cudaStream_t cs;
+    if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) {
+        set_error("tm_exec_create: stream");
+        return fail(TM_ECUDA);
+    }
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    int rc = TM_OK;
+    if (e == cudaSuccess) {
+        rc = enqueue(g, tr, args, P, x->scratch, counts, x->status, cs, nullptr);
+        cudaError_t e2 = cudaStreamEndCapture(cs, &graph);
+        if (rc == TM_OK && e2 != cudaSuccess) { set_error(std::string("capture: ") + cudaGetErrorString(e2)); rc = TM_ECUDA; }
+    } else {
+        set_error(std::string("capture: ") + cudaGetErrorString(e));
+        rc = TM_ECUDA;
+    }
+    if (rc == TM_OK && cudaGraphInstantiate(&x->exec, graph, 0) != cudaSuccess) {
+        set_error("tm_exec_create: graph instantiation");
+        rc = TM_ECUDA;
+    }
+    if (graph) cudaGraphDestroy(graph);
+    cudaStreamDestroy(cs);
+    if (rc != TM_OK) return fail(rc);
+    *out = x;
+    return TM_OK;
+}
+
+extern "C" int tm_exec_launch(tm_exec *x, void *stream) {
+    using namespace tmo;
+    if (!x) { set_error("tm_exec_launch: NULL"); return TM_EINVAL; }
+    TM_CUDA_TRY(cudaGraphLaunch(x->exec, (cudaStream_t)stream));
+    return TM_OK;
+}
+
+extern "C" int tm_exec_status(tm_exec *x, void *stream) {
+    using namespace tmo;
+    if (!x) { set_error("tm_exec_status: NULL"); return TM_EINVAL; }
+    int32_t st = 0;
+    TM_CUDA_TRY(cudaMemcpyAsync(&st, x->status, 4, cudaMemcpyDeviceToHost, (cudaStream_t)stream));
+    TM_CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
+    if (st) {
+        set_error("tm_exec: a bounded device wait expired in the last replay; its counts are incomplete");
+        return TM_ETIMEOUT;
+    }
+    return TM_OK;
+}
+
+extern "C" int tm_exec_free(tm_exec *x) {
+    if (!x) return TM_OK;
+    if (x->exec) cudaGraphExecDestroy(x->exec);
+    cudaFree(x->scratch);
+    cudaFree(x->status);
+    delete x;
+    return TM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Autotuner: times a small grid of launch shapes and split thresholds on the
+// caller's roots and keeps the fastest (coordinate descent, best of 2 runs).
+
+extern "C" int tm_autotune(const tm_graph *g, const tm_tree *tr, const tm_count_args *args, tm_tune *best,
+                           void *stream) {
+    using namespace tmo;
+    if (!g || !tr || !args || !best) { set_error("tm_autotune: NULL argument"); return TM_EINVAL; }
+    cudaStream_t s = (cudaStream_t)stream;
+    std::vector<int64_t> counts(tr->h.n_motifs);
+    tm_count_args a = *args;
+    a.flags &= ~TM_COUNTS_DEVICE;
+    auto timed = [&](const tm_count_args &c, float *ms) {
+        cudaEvent_t e0, e1;
+        cudaEventCreate(&e0);
+        cudaEventCreate(&e1);
+        float bestms = 1e30f;
+        int rc = TM_OK;
+        for (int rep = 0; rep < 2 && rc == TM_OK; rep++) {
+            cudaEventRecord(e0, s);
+            rc = mine(g, tr, &c, counts.data(), nullptr, s);
+            cudaEventRecord(e1, s);
+            cudaEventSynchronize(e1);
+            float t = 0;
+            cudaEventElapsedTime(&t, e0, e1);
+            bestms = std::min(bestms, t);
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        *ms = bestms;
+        return rc;
+    };
+    tm_tune cur{0, kDonateSeq, kDonateLeaf, kPollEvery, 0.f};
+    auto apply = [&](const tm_tune &t) {
+        tm_count_args c = a;
+        c.ctas_per_sm = t.ctas_per_sm;
+        c.donate_seq = t.donate_seq;
+        c.donate_leaf = t.donate_leaf;
+        c.poll_every = t.poll_every;
+        return c;
+    };
+    float cur_ms = 0;
+    TM_TRY(timed(apply(cur), &cur_ms));
+    const int ctas[] = {2, 3, 4};
+    const int seqs[] = {32, 64, 256, 1024};
+    const int leaves[] = {256, 1024, 4096};
+    const int polls[] = {1, 4, 16};
+    for (int pass = 0; pass < 2; pass++) {
+        for (int c : ctas) { tm_tune t = cur; t.ctas_per_sm = c; float ms; TM_TRY(timed(apply(t), &ms)); if (ms < cur_ms) { cur = t; cur_ms = ms; } }
+        if (!(a.mode & TM_SCHED_DYNAMIC)) break;
+        for (int v : seqs) { tm_tune t = cur; t.donate_seq = v; float ms; TM_TRY(timed(apply(t), &ms)); if (ms < cur_ms) { cur = t; cur_ms = ms; } }
+        for (int v : leaves) { tm_tune t = cur; t.donate_leaf = v; float ms; TM_TRY(timed(apply(t), &ms)); if (ms < cur_ms) { cur = t; cur_ms = ms; } }
+        for (int v : polls) { tm_tune t = cur; t.poll_every = v; float ms; TM_TRY(timed(apply(t), &ms)); if (ms < cur_ms) { cur = t; cur_ms = ms; } }
+    }
+    cur.ms = cur_ms;
+    *best = cur;
+    return TM_OK;
+}
 
 // ---------------------------------------------------------------------------
 // Allocation-free counting.
@@ -1163,6 +1423,11 @@ extern "C" int tm_count_noalloc(const tm_graph *g, const tm_tree *tr, const int3
         prm.dynamic = 0;
         prm.react = 0;
         prm.split = nullptr;
+        prm.poll_every = kPollEvery;
+        prm.donate_seq = kDonateSeq;
+        prm.donate_leaf = kDonateLeaf;
+        prm.pad2 = 0;
+        prm.root_qmask = nullptr;
         k_mine<false><<<blocks, kThreads, dyn_smem, s>>>(prm);
         TM_CUDA_TRY(cudaGetLastError());
     }

@@ -47,12 +47,14 @@ std::vector<Edge> canonical(const int8_t *uv, int m, int *n_vertices) {
 }
 
 void build_chain(const std::vector<Edge> &m, const std::vector<int32_t> &refs,
-                 const std::vector<int64_t> &deltas, int32_t n_motifs, HostTree *out) {
+                 const std::vector<int64_t> &deltas, const std::vector<int32_t> &queries, int32_t n_motifs,
+                 HostTree *out) {
     HostNode n;
     n.C = m;
     n.refs = refs;
     out->nodes = {n};
     out->motif_delta = deltas;
+    out->motif_query = queries;
     out->n_motifs = n_motifs;
     out->n_leaves = 1;
     out->depth = (int32_t)m.size();
@@ -68,6 +70,11 @@ void build_chain(const std::vector<Edge> &m, const std::vector<int32_t> &refs,
 }  // namespace
 
 int tree_build(const int8_t *uv, const int32_t *off, int32_t n, const int64_t *delta, tm_tree **out) {
+    return tree_build_q(uv, off, n, delta, nullptr, out);
+}
+
+int tree_build_q(const int8_t *uv, const int32_t *off, int32_t n, const int64_t *delta, const int32_t *query,
+                 tm_tree **out) {
     if (n < 1 || !uv || !off || !delta || !out) {
         set_error("tm_tree_build: need at least one motif and non-NULL arrays");
         return TM_EINVAL;
@@ -135,6 +142,11 @@ int tree_build(const int8_t *uv, const int32_t *off, int32_t n, const int64_t *d
     h.max_vertices = max_v;
     h.n_deltas = (int32_t)distinct.size();
     h.motif_delta.assign(delta, delta + n);
+    if (query) {
+        for (int i = 0; i < n; i++)
+            if (query[i] < 0 || query[i] > 63) { set_error("tree: query index outside 0..63"); return TM_EINVAL; }
+        h.motif_query.assign(query, query + n);
+    }
     std::vector<Edge> path;
     int cur = 0;
     while (trie[cur].refs.empty() && trie[cur].next.size() == 1) {
@@ -186,7 +198,7 @@ int tree_build(const int8_t *uv, const int32_t *off, int32_t n, const int64_t *d
         const HostNode &nd = h.nodes[i];
         if (nd.refs.empty()) continue;
         HostTree c;
-        build_chain(nd.C, nd.refs, h.motif_delta, n, &c);
+        build_chain(nd.C, nd.refs, h.motif_delta, h.motif_query, n, &c);
         tr->chains.push_back(c);
     }
     tr->dev[0].resize(1 + tr->chains.size());
@@ -213,11 +225,19 @@ void flatten(const HostTree &h, bool par_leaves, TreeImage *img) {
     ds.erase(std::unique(ds.begin(), ds.end()), ds.end());
     auto didx = [&](int64_t x) { return (int)(std::lower_bound(ds.begin(), ds.end(), x) - ds.begin()); };
 
-    // subtree max window
+    // subtree max window and subtree queries
+    auto qof = [&](int32_t r) { return h.motif_query.empty() ? 0 : h.motif_query[r]; };
     std::vector<int> dmax(nn, -1);
+    std::vector<uint64_t> qmask(nn, 0);
     for (int i = nn - 1; i >= 0; i--) {  // preorder: children after parents
-        for (int32_t r : h.nodes[i].refs) dmax[i] = std::max(dmax[i], didx(h.motif_delta[r]));
-        for (int32_t c : h.nodes[i].children) dmax[i] = std::max(dmax[i], dmax[c]);
+        for (int32_t r : h.nodes[i].refs) {
+            dmax[i] = std::max(dmax[i], didx(h.motif_delta[r]));
+            qmask[i] |= 1ull << qof(r);
+        }
+        for (int32_t c : h.nodes[i].children) {
+            dmax[i] = std::max(dmax[i], dmax[c]);
+            qmask[i] |= qmask[c];
+        }
     }
     auto nvb_of = [&](const std::vector<Edge> &C, int k) {
         int nv = 0;
@@ -277,6 +297,7 @@ void flatten(const HostTree &h, bool par_leaves, TreeImage *img) {
         for (int32_t c : nd.children)
             if (is_par(c) && is_star(c) && h.nodes[c].C.size() == nd.C.size() + 1) dn.flags |= kNodeStarKids;
         dn.dmax = (int8_t)std::max(dmax[i], 0);
+        dn.qmask = qmask[i];
         dn.parent = (int16_t)(nd.parent >= 0 ? newid[nd.parent] : -1);
         int n_par = 0, n_seq = 0;
         for (int32_t c : nd.children) {
@@ -298,7 +319,7 @@ void flatten(const HostTree &h, bool par_leaves, TreeImage *img) {
         }
         dn.ref_begin = (int16_t)refs.size();
         dn.n_ref = (int16_t)nd.refs.size();
-        for (int32_t r : nd.refs) refs.push_back(DevRef{r, didx(h.motif_delta[r])});
+        for (int32_t r : nd.refs) refs.push_back(DevRef{r, (int16_t)didx(h.motif_delta[r]), (int16_t)qof(r)});
     }
     size_t b_nodes = sizeof(DevNode) * nodes.size();
     size_t b_refs = sizeof(DevRef) * std::max<size_t>(refs.size(), 1);

@@ -305,6 +305,14 @@ MID = GraphSpec("mid-1m-20m", 1_000_000, 20_000_000, 1.6, "bursty", seed=3)
 BATCHED = GraphSpec("batched-5m-50m", 5_000_000, 50_000_000, 1.7, "bursty", seed=4)
 SERVING = GraphSpec("serving-20m-200m", 20_000_000, 200_000_000, 1.7, "bursty", seed=6)
 
+# The batched and serving sizes with milder endpoint skew.  Under
+# rank-frequency Zipf(1.7) one vertex carries 49 % of all endpoints and the
+# random motif sets' multi-edge and star motifs on hub pairs have more
+# matches per root than can be enumerated at any of their windows; with
+# Zipf(0.5) the top vertex carries 0.02 %.
+BATCHED_MILD = GraphSpec("batched-5m-50m-zipf0.5", 5_000_000, 50_000_000, 0.5, "bursty", seed=4)
+SERVING_MILD = GraphSpec("serving-20m-200m-zipf0.5", 20_000_000, 200_000_000, 0.5, "bursty", seed=6)
+
 TINY_DELTA = 10_000
 MID_DELTA = 3600
 
@@ -319,6 +327,15 @@ def make_graph(spec: GraphSpec, n_edges: int | None = None):
         span = spec.span_s if n_edges is None else max(1, int(spec.span_s * e / spec.n_edges))
         t = bursty_times(spec.seed, e, span_s=span)
     return sort_edges(src, dst, t)
+
+
+def serving_query(seed: int, n_edges: int, n_roots: int = 64):
+    """A serving request: 1..16 motifs of 2..5 edges, a log-uniform integer
+    window in [60, 86400] per request, and a seeded uniform root sample."""
+    ms = query_motifs(seed, hi_edges=5)
+    u = rand_uniform(seed, 14, 0, 1)[0]
+    delta = int(math.exp(math.log(60) + u * (math.log(86400) - math.log(60))))
+    return ms, delta, root_sample(seed, n_edges, n_roots)
 
 
 def batched_sets(n_sets: int = 64, base_seed: int = 1000):

@@ -75,7 +75,33 @@ class tm_count_args(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_uint32), ("flags", ctypes.c_uint32), ("roots", ctypes.c_void_p),
                 ("n_roots", ctypes.c_int64), ("root_lo", ctypes.c_int64), ("root_hi", ctypes.c_int64),
                 ("per_root_counts", ctypes.c_void_p), ("per_root_work", ctypes.c_void_p),
-                ("ctas_per_sm", ctypes.c_int32), ("reserved", ctypes.c_int32), ("root_split", ctypes.c_void_p)]
+                ("ctas_per_sm", ctypes.c_int32), ("reserved", ctypes.c_int32), ("root_split", ctypes.c_void_p),
+                ("poll_every", ctypes.c_int32), ("donate_seq", ctypes.c_int32), ("donate_leaf", ctypes.c_int32),
+                ("reserved2", ctypes.c_int32)]
+
+
+class tm_server_config(ctypes.Structure):
+    _fields_ = [("streams", ctypes.c_int32), ("max_batch", ctypes.c_int32), ("mem_budget", ctypes.c_int64),
+                ("mode", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
+
+
+class tm_request_stats(ctypes.Structure):
+    _fields_ = [("queue_ms", ctypes.c_double), ("latency_ms", ctypes.c_double), ("batch", ctypes.c_int32),
+                ("batch_size", ctypes.c_int32)]
+
+
+class tm_server_info(ctypes.Structure):
+    _fields_ = [("batches", ctypes.c_int64), ("requests_done", ctypes.c_int64), ("pending", ctypes.c_int64),
+                ("in_flight", ctypes.c_int64), ("admitted_bytes", ctypes.c_int64),
+                ("peak_admitted_bytes", ctypes.c_int64)]
+
+
+class tm_tune(ctypes.Structure):
+    _fields_ = [("ctas_per_sm", ctypes.c_int32), ("donate_seq", ctypes.c_int32), ("donate_leaf", ctypes.c_int32),
+                ("poll_every", ctypes.c_int32), ("ms", ctypes.c_float)]
+
+    def as_dict(self):
+        return {name: getattr(self, name) for name, _ in self._fields_}
 
 
 class tm_run_stats(ctypes.Structure):
@@ -93,6 +119,8 @@ EXPORTS = ("tm_graph_load", "tm_graph_get_info", "tm_graph_edges", "tm_graph_fre
            "tm_tree_get_info", "tm_tree_get_node", "tm_tree_free", "tm_count", "tm_count_noalloc",
            "tm_features", "tm_model_create", "tm_model_free", "tm_model_get_params", "tm_model_set_params",
            "tm_model_fit_norm", "tm_model_predict", "tm_model_loss_grad", "tm_model_train", "tm_plan",
+           "tm_exec_create", "tm_exec_launch", "tm_exec_status", "tm_exec_free", "tm_autotune",
+           "tm_server_open", "tm_server_submit", "tm_server_poll", "tm_server_get_info", "tm_server_close",
            "tm_last_error", "tm_version")
 
 
@@ -125,6 +153,16 @@ def lib():
         L.tm_model_loss_grad.argtypes = [P, P, P, i64, P, P, P]
         L.tm_model_train.argtypes = [P, P, P, i64, i32, i32, F, P, P]
         L.tm_plan.argtypes = [P, P, P, i64, ctypes.c_double, i32, P, P, P]
+        L.tm_exec_create.argtypes = [P, P, ctypes.POINTER(tm_count_args), P, P, ctypes.POINTER(P)]
+        L.tm_exec_launch.argtypes = [P, P]
+        L.tm_exec_status.argtypes = [P, P]
+        L.tm_exec_free.argtypes = [P]
+        L.tm_autotune.argtypes = [P, P, ctypes.POINTER(tm_count_args), ctypes.POINTER(tm_tune), P]
+        L.tm_server_open.argtypes = [P, ctypes.POINTER(tm_server_config), ctypes.POINTER(P)]
+        L.tm_server_submit.argtypes = [P, P, P, i32, P, P, i64, ctypes.POINTER(i64)]
+        L.tm_server_poll.argtypes = [P, i64, i32, P, ctypes.POINTER(tm_request_stats)]
+        L.tm_server_get_info.argtypes = [P, ctypes.POINTER(tm_server_info)]
+        L.tm_server_close.argtypes = [P]
         L.tm_last_error.restype = ctypes.c_char_p
         L.tm_version.restype = ctypes.c_char_p
         for name in EXPORTS:
@@ -243,13 +281,8 @@ def tm_tree_free(tr) -> None:
     _check(lib().tm_tree_free(tr))
 
 
-def tm_count(g, tr, mode: int = TM_COMINE, roots=None, root_lo: int = 0, root_hi: int = 0,
-             counts=None, per_root_counts=None, per_root_work=None, stats: bool = False,
-             stream=None, ctas_per_sm: int = 0, root_split=None):
-    """Counts of every motif (np.int64 array, or into the device tensor ``counts``).
-
-    Returns ``counts`` or ``(counts, stats_dict)`` when ``stats``.
-    """
+def _count_args(mode=TM_COMINE, roots=None, root_lo=0, root_hi=0, per_root_counts=None, per_root_work=None,
+                ctas_per_sm=0, root_split=None, tune=None):
     a = tm_count_args()
     a.mode = mode
     a.flags = 0
@@ -277,6 +310,23 @@ def tm_count(g, tr, mode: int = TM_COMINE, roots=None, root_lo: int = 0, root_hi
             raise TypeError("root_split must be a CUDA tensor")
         keep.append(k)
         a.root_split = p
+    if tune is not None:
+        a.ctas_per_sm = tune["ctas_per_sm"]
+        a.donate_seq = tune["donate_seq"]
+        a.donate_leaf = tune["donate_leaf"]
+        a.poll_every = tune["poll_every"]
+    return a, keep
+
+
+def tm_count(g, tr, mode: int = TM_COMINE, roots=None, root_lo: int = 0, root_hi: int = 0,
+             counts=None, per_root_counts=None, per_root_work=None, stats: bool = False,
+             stream=None, ctas_per_sm: int = 0, root_split=None, tune=None):
+    """Counts of every motif (np.int64 array, or into the device tensor ``counts``).
+
+    Returns ``counts`` or ``(counts, stats_dict)`` when ``stats``.
+    """
+    a, keep = _count_args(mode, roots, root_lo, root_hi, per_root_counts, per_root_work, ctas_per_sm,
+                          root_split, tune)
     n_motifs = tm_tree_get_info(tr)["n_motifs"]
     if counts is None:
         out = np.zeros(n_motifs, np.int64)
@@ -308,6 +358,93 @@ def tm_count_noalloc(g, tr, counts, roots=None, root_lo: int = 0, root_hi: int =
         n = len(keep_r)
     _check(lib().tm_count_noalloc(g, tr, pr, n, root_lo, root_hi, pc, _stream(stream)))
     return counts
+
+
+class Exec:
+    """A count captured once in a CUDA graph (tm_exec); counts land in ``counts``."""
+
+    def __init__(self, g, tr, counts, stream=None, **kw):
+        a, self._keep = _count_args(**kw)
+        pc = _dev(counts, np.int64, "counts")
+        self.counts = counts
+        self.h = ctypes.c_void_p()
+        _check(lib().tm_exec_create(g, tr, ctypes.byref(a), pc, _stream(stream), ctypes.byref(self.h)))
+
+    def launch(self, stream=None):
+        _check(lib().tm_exec_launch(self.h, _stream(stream)))
+
+    def status(self, stream=None):
+        _check(lib().tm_exec_status(self.h, _stream(stream)))
+
+    def close(self):
+        if getattr(self, "h", None) is not None and _lib is not None:
+            _check(lib().tm_exec_free(self.h))
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """Owning wrapper of a tm_server (continuous batching over a resident graph)."""
+
+    def __init__(self, graph, streams: int = 2, max_batch: int = 32, mem_budget: int = 4 << 30,
+                 mode: int = TM_SCHED_DYNAMIC):
+        self.graph = graph
+        cfg = tm_server_config(streams, max_batch, mem_budget, mode, 0)
+        self.h = ctypes.c_void_p()
+        _check(lib().tm_server_open(graph.h, ctypes.byref(cfg), ctypes.byref(self.h)))
+        self.n_motifs = {}
+
+    def submit(self, motifs, deltas, roots) -> int:
+        uv, off = motif_arrays(motifs)
+        d = np.broadcast_to(np.asarray(deltas, np.int64), (len(motifs),)).copy()
+        r = np.ascontiguousarray(roots, np.int32)
+        tk = ctypes.c_int64(0)
+        _check(lib().tm_server_submit(self.h, uv.ctypes.data_as(ctypes.c_void_p), off.ctypes.data_as(ctypes.c_void_p),
+                                      len(motifs), d.ctypes.data_as(ctypes.c_void_p),
+                                      r.ctypes.data_as(ctypes.c_void_p), len(r), ctypes.byref(tk)))
+        self.n_motifs[tk.value] = len(motifs)
+        return tk.value
+
+    def poll(self, ticket: int, wait: bool = False):
+        """None while pending, else (counts, stats dict)."""
+        out = np.zeros(self.n_motifs[ticket], np.int64)
+        st = tm_request_stats()
+        rc = lib().tm_server_poll(self.h, ticket, 1 if wait else 0, out.ctypes.data_as(ctypes.c_void_p),
+                                  ctypes.byref(st))
+        if rc == 0:
+            return None
+        if rc < 0:
+            raise TMError(rc, tm_last_error())
+        del self.n_motifs[ticket]
+        return out, {name: getattr(st, name) for name, _ in st._fields_}
+
+    def info(self) -> dict:
+        i = tm_server_info()
+        _check(lib().tm_server_get_info(self.h, ctypes.byref(i)))
+        return {name: getattr(i, name) for name, _ in i._fields_}
+
+    def close(self):
+        if getattr(self, "h", None) is not None and _lib is not None:
+            _check(lib().tm_server_close(self.h))
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def tm_autotune(g, tr, stream=None, **kw) -> dict:
+    a, keep = _count_args(**kw)
+    t = tm_tune()
+    _check(lib().tm_autotune(g, tr, ctypes.byref(a), ctypes.byref(t), _stream(stream)))
+    return t.as_dict()
 
 
 # ------------------------------------------------------------------ learned scheduling
