@@ -285,6 +285,7 @@ def run_serving(args):
     src, dst, t = synth.make_graph(spec)
     t_gen = time.perf_counter() - t0
     g = tmotif.Graph(src, dst, t, spec.n_nodes, presorted=True)
+    print("graph generated in %.1f s" % t_gen, file=sys.stderr, flush=True)
     rate = args.rate
     n_req = int(rate * args.duration)
     rng = np.random.default_rng(7 + rank)
@@ -303,6 +304,8 @@ def run_serving(args):
             if arrivals[i] > now:
                 time.sleep(arrivals[i] - now)
             tickets.append(srv.submit(*q))
+        print("submitted %d requests in %.1f s" % (len(tickets), time.perf_counter() - start), file=sys.stderr,
+              flush=True)
         res = [srv.poll(tk, wait=True) for tk in tickets]
         end = time.perf_counter()
     info = srv.info()

@@ -266,6 +266,19 @@ __global__ void k_adj(const int32_t *eids, const int32_t *other, int64_t n, int2
     }
 }
 
+// after[e] = first position in the list of vertex key[e] whose edge id exceeds e
+__global__ void k_after(const int32_t *key, int64_t n, const int64_t *off, const int2 *adj, int32_t *after) {
+    int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n) return;
+    const int32_t x = key[e];
+    int64_t lo = off[x], hi = off[x + 1];
+    while (lo < hi) {
+        int64_t mid = (lo + hi) >> 1;
+        if (adj[mid].y <= (int32_t)e) lo = mid + 1; else hi = mid;
+    }
+    after[e] = (int32_t)lo;
+}
+
 __global__ void k_pair_starts(const int32_t *pe, int64_t n, const int32_t *src, const int32_t *dst,
                               int32_t *flag) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -542,6 +555,18 @@ static int graph_build_impl(const int32_t *src_in, const int32_t *dst_in, const 
         k_pair_pos<<<grid(E), 256, 0, s>>>(pair_eid, E, starts, n_pairs, pr_pos, pr_end);
         TM_CUDA_TRY(cudaGetLastError());
     }
+    int32_t *a_os, *a_od, *a_is, *a_id;
+    TM_TRY(keep(g, &a_os, E));
+    TM_TRY(keep(g, &a_od, E));
+    TM_TRY(keep(g, &a_is, E));
+    TM_TRY(keep(g, &a_id, E));
+    if (E > 0) {
+        k_after<<<grid(E), 256, 0, s>>>(src, E, out_off, out_adj, a_os);
+        k_after<<<grid(E), 256, 0, s>>>(dst, E, out_off, out_adj, a_od);
+        k_after<<<grid(E), 256, 0, s>>>(src, E, in_off, in_adj, a_is);
+        k_after<<<grid(E), 256, 0, s>>>(dst, E, in_off, in_adj, a_id);
+        TM_CUDA_TRY(cudaGetLastError());
+    }
     unsigned long long *mx;
     TM_TRY(sc.get(&mx, 2));
     TM_CUDA_TRY(cudaMemsetAsync(mx, 0, 2 * sizeof(unsigned long long), s));
@@ -561,6 +586,10 @@ static int graph_build_impl(const int32_t *src_in, const int32_t *dst_in, const 
     d.pair_eid = pair_eid;
     d.pr_pos = pr_pos;
     d.pr_end = pr_end;
+    d.after_os = a_os;
+    d.after_od = a_od;
+    d.after_is = a_is;
+    d.after_id = a_id;
     d.pair_tab = tab;
     d.pair_mask = cap - 1;
     g->n_pairs = n_pairs;

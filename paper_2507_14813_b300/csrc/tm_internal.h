@@ -45,6 +45,11 @@ struct DevGraph {
     const int32_t *pair_eid;  // eids ordered by (src, dst, eid)
     const int32_t *pr_pos;    // by eid: position of the edge in pair_eid
     const int32_t *pr_end;    // by eid: end of its (src, dst) run in pair_eid
+    // by eid e: position in a list of the first entry after e (absolute index)
+    const int32_t *after_os;  // in out(src e)
+    const int32_t *after_od;  // in out(dst e)
+    const int32_t *after_is;  // in in(src e)
+    const int32_t *after_id;  // in in(dst e)
     const ulonglong2 *pair_tab; // open-addressing table: x = key (src<<32|dst), y = start | len<<32
     uint64_t pair_mask;       // table capacity - 1 (power of two)
 };
@@ -111,6 +116,7 @@ struct DevTree {
     const DevNode *nodes;
     const DevRef *refs;
     const int64_t *deltas;   // distinct windows, ascending
+    const int8_t *qdmax;     // per query 0..63: largest window index of its refs (-1: none)
     int32_t n_nodes;
     int32_t n_refs;
     int32_t n_deltas;
@@ -144,7 +150,7 @@ namespace tmo {
 // at o_refs, then the window table at o_deltas (offsets 256-byte aligned).
 struct TreeImage {
     std::vector<char> bytes;
-    size_t o_refs = 0, o_deltas = 0;
+    size_t o_refs = 0, o_deltas = 0, o_qdmax = 0;
     int32_t n_nodes = 0, n_refs = 0, n_deltas = 0, n_counters = 0;
 };
 DevTree image_tree(const TreeImage &img, const void *dev);

@@ -47,6 +47,7 @@ constexpr int kWarps = 8;                 // warps per CTA
 constexpr int kThreads = kWarps * 32;
 constexpr int kSmemCounters = 2048;       // per-CTA counters kept in shared memory up to this many
 constexpr int kLaneScanMax = 24;          // leaf windows up to this size are scanned by the lane
+constexpr uint32_t kCacheEmpty = 0xffffffffu;
 
 constexpr int kQueueCap = 1 << 20;        // tasks per launch (slots are not reused)
 constexpr int kPollEvery = 4;             // default: chunk loads between looks at the idle counter
@@ -120,9 +121,12 @@ struct WarpState {
     int16_t sib_end[kMaxE];
     int8_t ltype[kMaxE];
     int8_t seq[kMaxE];        // survivors of level k are descended (not only counted)
-    int8_t star[kMaxE];       // suf[k] is kept (star leaves are counted from level k)
+    int8_t star[kMaxE];       // star leaves are counted from level k: scanned top-down, suf[k] kept
     int64_t wend[kMaxE];      // end of level k's window (a donated slice may end earlier)
-    int64_t suf[kMaxE];       // survivors of level k from the current chunk to wend
+    int64_t suf[kMaxE];       // star frames: survivors of level k above the scan cursor, up to wend
+    uint32_t ckey[64];        // later-occurrence counts per candidate endpoint, for one star frame
+    uint32_t cval[64];
+    int32_t cache_owner;      // level whose star frame owns ckey/cval, or -1
     int32_t m2g[kMaxV];
     int32_t ehi[TM_MAX_DELTAS];
 };
@@ -180,7 +184,62 @@ __device__ __forceinline__ int64_t lane_upper_e(const int32_t *__restrict__ a, i
     return lo;
 }
 
+// first position in adj[lo, hi) whose edge id exceeds key, galloping from lo; per lane
+__device__ __forceinline__ int64_t lane_gallop(const int2 *__restrict__ adj, int64_t lo, int64_t hi, int32_t key,
+                                               unsigned long long &probes) {
+    if (lo >= hi) return lo;
+    probes++;
+    if (__ldg(&adj[lo].y) > key) return lo;
+    int64_t a = lo, step = 1, b = hi;          // adj[a].y <= key; answer in (a, b]
+    while (true) {
+        int64_t q = a + step;
+        if (q >= hi) break;
+        probes++;
+        if (__ldg(&adj[q].y) <= key) { a = q; step <<= 1; } else { b = q; break; }
+    }
+    while (b - a > 1) {
+        int64_t mid = a + ((b - a) >> 1);
+        probes++;
+        if (__ldg(&adj[mid].y) <= key) a = mid; else b = mid;
+    }
+    return b;
+}
+
+// First position in the list of x after edge `last`, when x is an endpoint of
+// `last` (per-edge index), else -1.
+__device__ __forceinline__ int64_t after_pos(const DevGraph &g, bool out, int32_t x, int32_t last, int32_t s,
+                                             int32_t d) {
+    if (out) {
+        if (x == s) return __ldg(g.after_os + last);
+        if (x == d) return __ldg(g.after_od + last);
+    } else {
+        if (x == d) return __ldg(g.after_id + last);
+        if (x == s) return __ldg(g.after_is + last);
+    }
+    return -1;
+}
+
 // first position in adj[lo, hi) whose edge id exceeds key; warp-cooperative
+__device__ int64_t warp_upper(const int2 *__restrict__ adj, int64_t lo, int64_t hi, int32_t key, int lane,
+                              unsigned long long &probes);
+
+// the same, galloping from lo: one round of probes at lo + 2^lane - 1 brackets
+// the answer, then the 32-ary search narrows it
+__device__ int64_t warp_gallop(const int2 *__restrict__ adj, int64_t lo, int64_t hi, int32_t key, int lane,
+                               unsigned long long &probes) {
+    if (hi - lo <= 32) return warp_upper(adj, lo, hi, key, lane, probes);
+    int64_t q = lane == 31 ? hi - 1 : lo + ((int64_t)1 << lane) - 1;
+    if (q > hi - 1) q = hi - 1;
+    const bool gt = __ldg(&adj[q].y) > key;
+    probes += 1;
+    const uint32_t b = __ballot_sync(0xffffffffu, gt);
+    if (b == 0) return hi;
+    const int f = __ffs(b) - 1;
+    const int64_t qf = __shfl_sync(0xffffffffu, q, f);
+    const int64_t qp = __shfl_sync(0xffffffffu, q, f > 0 ? f - 1 : 0);
+    return warp_upper(adj, f > 0 ? qp + 1 : lo, qf, key, lane, probes) ;
+}
+
 __device__ int64_t warp_upper(const int2 *__restrict__ adj, int64_t lo, int64_t hi, int32_t key, int lane,
                               unsigned long long &probes) {
     while (hi - lo > 32) {
@@ -268,9 +327,10 @@ struct Miner {
     int polls;                         // chunk loads since the last look at the idle counter
     int split_h;                       // planned slices for the current root's first-level lists
     uint64_t rmask;                    // queries served by the current root
+    int32_t cap;                       // last edge id any of those queries' windows reaches
 
     __device__ Miner(const Params &pp, WarpState &s, unsigned long long *c, int l)
-        : p(pp), ws(s), s_cnt(c), lane(l), polls(0), split_h(0), rmask(~0ull) {
+        : p(pp), ws(s), s_cnt(c), lane(l), polls(0), split_h(0), rmask(~0ull), cap(INT32_MAX) {
         for (int i = 0; i < kStatFields; i++) w.v[i] = 0;
     }
 
@@ -313,8 +373,9 @@ struct Miner {
             const int2 *adj = out ? g.out_adj : g.in_adj;
             const int64_t *off = out ? g.out_off : g.in_off;
             int64_t b0 = __ldg(off + x), b1 = __ldg(off + x + 1);
-            int64_t a = lane_upper(adj, b0, b1, last, lp);
-            int64_t b = lane_upper(adj, a, b1, hi, lp);
+            int64_t a = after_pos(g, out, x, last, cs, cd);
+            if (a < 0) a = lane_upper(adj, b0, b1, last, lp);
+            int64_t b = lane_gallop(adj, a, b1, hi, lp);
             if (b - a <= kLaneScanMax) {
                 for (int64_t i = a; i < b; i++) {
                     int32_t y = __ldg(&adj[i].x);
@@ -347,23 +408,31 @@ struct Miner {
     // A star leaf whose window is the frame's own counts from the frame:
     // the later survivors of level k (suffix count `suf` of the chunk) minus
     // the later edges of the lane's own (src, dst) run inside the window.
+    // S: lanes that evaluate; Sall: every survivor of the chunk (for the star count).
     __device__ void leaf_batch(const DevNode &L, int k, uint32_t S, int uk, int vk, int32_t cs, int32_t cd,
-                               int32_t last, int frame_dmax, int64_t suf) {
+                               int32_t last, int32_t fhi, int64_t suf, int32_t y, uint32_t peers, uint32_t Sall) {
         const bool star = (L.flags & kNodeStarLeaf) && ws.star[k];
-        const uint32_t le = (lane == 31) ? 0xffffffffu : ((2u << lane) - 1u);   // lanes <= this one
+        const uint32_t above = (lane == 31) ? 0u : ~((2u << lane) - 1u);       // lanes after this one
         for (int i = 0; i < L.n_ref; i++) {
             const DevRef ref = p.tr.refs[L.ref_begin + i];
             if (!((rmask >> ref.query) & 1ull)) continue;
             const int32_t hi = ws.ehi[ref.delta];
             unsigned long long c = 0;
             if (((S >> lane) & 1u) && last < hi) {
-                if (star && ref.delta == frame_dmax) {
+                if (star && hi == fhi) {
                     unsigned long long pr = 0;
-                    const int64_t later = suf - __popc(S & le);
-                    const int64_t same = run_tail(p.g.pair_eid, __ldg(p.g.pr_pos + last), __ldg(p.g.pr_end + last), hi, pr);
+                    const int64_t later = suf + __popc(Sall & above);
+                    int64_t same;
+                    const uint32_t slot = ((uint32_t)y * 2654435761u) >> 26;
+                    if (ws.cache_owner == k && ws.ckey[slot] == (uint32_t)y) {
+                        same = (int64_t)ws.cval[slot] + __popc(peers & above);
+                    } else {
+                        same = run_tail(p.g.pair_eid, __ldg(p.g.pr_pos + last), __ldg(p.g.pr_end + last), hi, pr);
+                        pr += 2;
+                    }
                     c = (unsigned long long)(later - same);
                     if (kStats) {
-                        w.v[kStPairProbe] += pr + 2;
+                        w.v[kStPairProbe] += pr;
                         w.v[kStLeaf] += 1;
                     }
                 } else {
@@ -380,6 +449,7 @@ struct Miner {
     // the survivors to descend.
     __device__ uint32_t survivors(int k, const DevNode &N, uint32_t S, int2 c, int64_t suf) {
         if (S == 0) return 0;
+        const uint32_t peers = ws.star[k] ? __match_any_sync(0xffffffffu, ((S >> lane) & 1u) ? c.x : -1) : 0u;
         const int uk = N.eu[k], vk = N.ev[k];
         int32_t cs, cd;
         const int8_t lt = ws.ltype[k];
@@ -403,14 +473,14 @@ struct Miner {
             for (int ci = 0; ci < N.n_par; ci++) {
                 const DevNode L = p.tr.nodes[N.child_begin + N.n_seq + ci];
                 if (!(L.qmask & rmask)) continue;
-                uint32_t S2 = __ballot_sync(0xffffffffu, c.y < ws.ehi[L.dmax]) & S;
-                if (S2) leaf_batch(L, k, S2, uk, vk, cs, cd, c.y, N.dmax, suf);
+                uint32_t S2 = __ballot_sync(0xffffffffu, c.y < min(ws.ehi[L.dmax], cap)) & S;
+                if (S2) leaf_batch(L, k, S2, uk, vk, cs, cd, c.y, frame_hi(N), suf, c.x, peers, S);
             }
         }
         const bool par_self = (N.flags & kNodeParLeaf) && (k == N.k_end - 2);
         if (par_self) {
-            uint32_t S2 = __ballot_sync(0xffffffffu, c.y < ws.ehi[N.dmax]) & S;
-            if (S2) leaf_batch(N, k, S2, uk, vk, cs, cd, c.y, N.dmax, suf);
+            uint32_t S2 = __ballot_sync(0xffffffffu, c.y < frame_hi(N)) & S;
+            if (S2) leaf_batch(N, k, S2, uk, vk, cs, cd, c.y, frame_hi(N), suf, c.x, peers, S);
         }
         return ws.seq[k] ? S : 0u;
     }
@@ -461,24 +531,60 @@ struct Miner {
                ((N.flags & kNodeStarKids) && k == N.k_end - 1);
     }
 
-    // Survivors of level k of node N in [pos, wend) (the filter of load_chunk).
-    __device__ int64_t count_survivors(const DevNode &N, int k, int8_t lt, int64_t pos, int64_t wend) {
+    // The per-warp table of later-occurrence counts belongs to the star
+    // frame at level k from now on (empty), if no other frame holds it.
+    __device__ void cache_claim(int k) {
+        if (ws.cache_owner >= 0) return;
+        __syncwarp();
+        ws.ckey[lane] = kCacheEmpty;
+        ws.ckey[lane + 32] = kCacheEmpty;
+        if (lane == 0) ws.cache_owner = k;
+        __syncwarp();
+    }
+
+    __device__ void cache_release(int k) {
+        __syncwarp();
+        if (lane == 0 && ws.cache_owner == k) ws.cache_owner = -1;
+        __syncwarp();
+    }
+
+    // Add the survivors of one chunk (groups of equal endpoint `peers`) to the table.
+    __device__ void cache_add(uint32_t S, int32_t y, uint32_t peers) {
+        if ((S >> lane) & 1u) {
+            if (lane == __ffs(peers) - 1) {
+                const uint32_t slot = ((uint32_t)y * 2654435761u) >> 26;
+                const uint32_t key = ws.ckey[slot];
+                const uint32_t n = (uint32_t)__popc(peers);
+                if (key == (uint32_t)y) ws.cval[slot] += n;
+                else if (key == kCacheEmpty && atomicCAS(&ws.ckey[slot], kCacheEmpty, (uint32_t)y) == kCacheEmpty)
+                    ws.cval[slot] = n;
+            }
+        }
+        __syncwarp();
+    }
+
+    // Survivors of level k of node N in [pos, wend) (the filter of load_chunk);
+    // with `fill`, also their endpoints into the table this frame owns.
+    __device__ int64_t count_survivors(const DevNode &N, int k, int8_t lt, int64_t pos, int64_t wend, bool fill) {
         const int2 *adj = lt == kListOut ? p.g.out_adj : p.g.in_adj;
         const int32_t last = ws.eid[k - 1];
-        const int32_t hi = ws.ehi[N.dmax];
+        const int32_t hi = frame_hi(N);
         const int nv = N.nvb[k];
         int64_t n = 0;
         for (int64_t b = pos; b < wend; b += 32) {
             const int64_t i = b + lane;
             bool ok = false;
+            int2 c = make_int2(0, 0);
             if (i < wend) {
-                const int2 c = __ldg(adj + i);
+                c = __ldg(adj + i);
                 bool bad = false;
 #pragma unroll
                 for (int l = 0; l < kMaxV; l++) bad |= (l < nv) & (c.x == ws.m2g[l]);
                 ok = !bad && c.y > last && c.y <= hi;
             }
-            n += __popc(__ballot_sync(0xffffffffu, ok));
+            const uint32_t S = __ballot_sync(0xffffffffu, ok);
+            n += __popc(S);
+            if (fill) cache_add(S, c.x, __match_any_sync(0xffffffffu, ok ? c.x : -1));
             if (kStats && lane == 0) w.v[kStCand] += (unsigned long long)((wend - b) < 32 ? (wend - b) : 32);
         }
         return n;
@@ -487,13 +593,14 @@ struct Miner {
     // Open level k for node `node` (siblings up to sib_end): the slice of
     // its list with edge ids in (eid[k-1], ehi].
     __device__ void open(int k, int node, int sib_end) {
+        cache_release(k);                               // a sibling re-opening this level
         const DevNode N = p.tr.nodes[node];
         if (!(N.qmask & rmask)) {                       // no query of this root below this node
             set_frame(k, node, sib_end, kListGlobal, 0, 0, 0, false, 0, false, 0);
             return;
         }
         const int32_t last = ws.eid[k - 1];
-        const int32_t hi = ws.ehi[N.dmax];
+        const int32_t hi = frame_hi(N);
         int8_t lt;
         int32_t x;
         list_of(N, k, lt, x);
@@ -505,14 +612,16 @@ struct Miner {
             const int64_t *off = lt == kListOut ? p.g.out_off : p.g.in_off;
             const int2 *adj = lt == kListOut ? p.g.out_adj : p.g.in_adj;
             const int64_t b0 = __ldg(off + x), b1 = __ldg(off + x + 1);
-            if (ws.ltype[k - 1] == lt && ws.lvert[k - 1] == x) start = ws.mpos[k - 1] + 1;  // same list as above
+            // the list of an endpoint of the previous match starts right after it (per-edge index)
+            const int64_t ap = after_pos(p.g, lt == kListOut, x, last, ws.m2g[N.eu[k - 1]], ws.m2g[N.ev[k - 1]]);
+            if (ap >= 0) start = ap;
             else if (b1 - b0 <= 32) start = b0;                 // the chunk mask drops ids <= last
             else start = warp_upper(adj, b0, b1, last, lane, w.v[kStListProbe]);
-            end = (b1 - start <= 32) ? b1 : warp_upper(adj, start, b1, hi, lane, w.v[kStListProbe]);
+            end = (b1 - start <= 32) ? b1 : warp_gallop(adj, start, b1, hi, lane, w.v[kStListProbe]);
         }
         const bool star = lt != kListGlobal && star_of(N, k);
-        const int64_t suf = star ? count_survivors(N, k, lt, start, end) : 0;
-        set_frame(k, node, sib_end, lt, x, start, end, seq_of(N, k), end, star, suf);
+        set_frame(k, node, sib_end, lt, x, start, end, seq_of(N, k), end, star, 0);
+        if (star) cache_claim(k);
         if (kStats && lane == 0) w.v[kStExp]++;
         if (k == 1 && split_h > 1) force_split(k, split_h);
     }
@@ -525,6 +634,15 @@ struct Miner {
         if (rem <= 32) return;
         int64_t sz = (rem + parts - 1) / parts;
         sz = (sz + 31) & ~31ll;
+        if (ws.star[k]) {                              // scanned top-down: keep the top slice
+            const int64_t keep = end - sz;
+            for (int64_t lo = pos; lo < keep; lo += sz)
+                if (!push_task(k, lo, min(keep, lo + sz))) return;
+            __syncwarp();
+            if (lane == 0) ws.pos[k] = keep;
+            __syncwarp();
+            return;
+        }
         for (int64_t lo = pos + sz; lo < end; lo += sz)
             if (!push_task(k, lo, min(end, lo + sz))) return;
         __syncwarp();
@@ -578,7 +696,13 @@ struct Miner {
             const int64_t rem = end - pos;
             if (rem < (ws.seq[kb] ? p.donate_seq : p.donate_leaf)) continue;
             const int64_t mid = pos + (((rem >> 1) + 31) & ~31ll);
-            if (push_task(kb, mid, end)) {
+            if (ws.star[kb]) {                         // scanned top-down: hand over the bottom part
+                if (push_task(kb, pos, mid)) {
+                    __syncwarp();
+                    if (lane == 0) ws.pos[kb] = mid;
+                    __syncwarp();
+                }
+            } else if (push_task(kb, mid, end)) {
                 __syncwarp();
                 if (lane == 0) ws.end[kb] = mid;
                 __syncwarp();
@@ -660,17 +784,31 @@ struct Miner {
             if (kStats) w.v[kStListProbe] += pr;
         }
         __syncwarp();
+        // with request masks, no frame of this root scans past its own requests' largest window
+        cap = INT32_MAX;
+        if (rmask != ~0ull) {
+            int32_t c = -1;
+            const int q = lane, q2 = lane + 32;
+            if ((rmask >> q) & 1ull) { const int d = p.tr.qdmax[q]; if (d >= 0) c = max(c, ws.ehi[d]); }
+            if ((rmask >> q2) & 1ull) { const int d = p.tr.qdmax[q2]; if (d >= 0) c = max(c, ws.ehi[d]); }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) c = max(c, __shfl_xor_sync(0xffffffffu, c, o));
+            cap = c < 0 ? INT32_MAX : c;
+        }
     }
+
+    __device__ __forceinline__ int32_t frame_hi(const DevNode &N) const { return min(ws.ehi[N.dmax], cap); }
 
     // Load and filter the next chunk of level k.
     __device__ void load_chunk(int k) {
         const DevNode N = p.tr.nodes[ws.node[k]];
         const int8_t lt = ws.ltype[k];
-        const int64_t base = ws.pos[k];
-        const int64_t i = base + lane;
+        const bool down = ws.star[k];                   // star frames run from the top
         const int64_t end = ws.end[k];
+        const int64_t base = down ? max(ws.pos[k], end - 32) : ws.pos[k];
+        const int64_t i = base + lane;
         const int32_t last = ws.eid[k - 1];
-        const int32_t hi = ws.ehi[N.dmax];
+        const int32_t hi = frame_hi(N);
         bool valid = i < end;
         int2 c = make_int2(0, 0);
         if (valid) {
@@ -707,10 +845,16 @@ struct Miner {
         __syncwarp();
         if (lane == 0) {
             ws.cbase[k] = base;
-            ws.pos[k] = outw ? end : base + 32;
-            ws.suf[k] = suf - __popc(S);
+            if (down) {
+                ws.end[k] = base;
+                ws.suf[k] = suf + __popc(S);
+            } else {
+                ws.pos[k] = outw ? end : base + 32;
+            }
         }
         uint32_t D = survivors(k, N, S, c, suf);
+        if (down && ws.cache_owner == k)
+            cache_add(S, c.x, __match_any_sync(0xffffffffu, ((S >> lane) & 1u) ? c.x : -1));
         __syncwarp();
         if (lane == 0) ws.mask[k] = D;
         __syncwarp();
@@ -763,6 +907,7 @@ struct Miner {
                 open(k, ws.node[k] + 1, ws.sib_end[k]);
                 continue;
             }
+            cache_release(k);
             k--;
         }
     }
@@ -773,6 +918,7 @@ struct Miner {
         const int32_t a = __ldg(g.src + r), b = __ldg(g.dst + r);
         if (a == b) return;                             // injective map needs a != b
         windows(r);
+        if (lane == 0) ws.cache_owner = -1;
         const DevNode N0 = p.tr.nodes[0];
         set_frame(0, 0, 1, kListGlobal, -1, 0, 0, seq_of(N0, 0), 0, false, 0);
         if (lane == 0) ws.cbase[0] = r;
@@ -806,7 +952,11 @@ struct Miner {
         int32_t x;
         list_of(N, k, lt, x);
         const bool star = lt != kListGlobal && star_of(N, k);
-        const int64_t suf = star ? count_survivors(N, k, lt, tk.lo, tk.wend) : 0;
+        if (lane == 0) ws.cache_owner = -1;
+        __syncwarp();
+        if (star) cache_claim(k);
+        // a top-down slice needs the survivors above it, up to the window's end
+        const int64_t suf = star ? count_survivors(N, k, lt, tk.hi, tk.wend, true) : 0;
         set_frame(k, tk.node, tk.node + 1, lt, x, tk.lo, tk.hi, seq_of(N, k), tk.wend, star, suf);
         run(k);
     }

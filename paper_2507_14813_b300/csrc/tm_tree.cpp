@@ -321,12 +321,16 @@ void flatten(const HostTree &h, bool par_leaves, TreeImage *img) {
         dn.n_ref = (int16_t)nd.refs.size();
         for (int32_t r : nd.refs) refs.push_back(DevRef{r, (int16_t)didx(h.motif_delta[r]), (int16_t)qof(r)});
     }
+    std::vector<int8_t> qd(64, -1);
+    for (const DevRef &r : refs) qd[r.query] = (int8_t)std::max<int>(qd[r.query], r.delta);
     size_t b_nodes = sizeof(DevNode) * nodes.size();
     size_t b_refs = sizeof(DevRef) * std::max<size_t>(refs.size(), 1);
     size_t b_ds = sizeof(int64_t) * std::max<size_t>(ds.size(), 1);
     img->o_refs = (b_nodes + 255) / 256 * 256;
     img->o_deltas = img->o_refs + (b_refs + 255) / 256 * 256;
-    img->bytes.assign(img->o_deltas + b_ds, 0);
+    img->o_qdmax = img->o_deltas + (b_ds + 255) / 256 * 256;
+    img->bytes.assign(img->o_qdmax + 64, 0);
+    memcpy(img->bytes.data() + img->o_qdmax, qd.data(), 64);
     memcpy(img->bytes.data(), nodes.data(), b_nodes);
     if (!refs.empty()) memcpy(img->bytes.data() + img->o_refs, refs.data(), sizeof(DevRef) * refs.size());
     if (!ds.empty()) memcpy(img->bytes.data() + img->o_deltas, ds.data(), sizeof(int64_t) * ds.size());
@@ -363,6 +367,7 @@ DevTree image_tree(const TreeImage &img, const void *dev) {
     d.nodes = (const DevNode *)b;
     d.refs = (const DevRef *)(b + img.o_refs);
     d.deltas = (const int64_t *)(b + img.o_deltas);
+    d.qdmax = (const int8_t *)(b + img.o_qdmax);
     d.n_nodes = img.n_nodes;
     d.n_refs = img.n_refs;
     d.n_deltas = img.n_deltas;

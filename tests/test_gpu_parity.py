@@ -285,3 +285,33 @@ def test_mid_config_heavy_star_leaves_vs_scan(mid):
     b = tmotif.count(g, tr, roots=roots, mode=D | tmotif.TM_LEAF_SCAN)
     assert a.tolist() == b.tolist()
     assert st["tasks_split"] > 0
+
+
+NESTED_STARS = [((0, 1), (0, 2), (0, 3)),
+                ((0, 1), (0, 2), (1, 3), (1, 4)),
+                ((0, 1), (0, 2), (1, 3), (3, 0)),
+                ((0, 1), (2, 1), (3, 1)),
+                ((0, 1), (2, 1), (0, 3), (4, 3))]
+
+
+@pytest.mark.parametrize("mode", [0, D, tmotif.TM_PERMOTIF | D])
+def test_nested_star_frames(tiny, mode):
+    """A star frame owns the per-warp count table while a deeper star frame
+    (nested under it) counts its stars from the pair index instead."""
+    src, dst, t, g, _ = tiny
+    tr = tmotif.Tree(NESTED_STARS, synth.TINY_DELTA)
+    want = [oracle.count_motif(src, dst, t, m, synth.TINY_DELTA) for m in NESTED_STARS]
+    assert tmotif.count(g, tr, mode=mode).tolist() == want
+
+
+def test_nested_star_frames_mid_split(mid):
+    import torch
+    src, dst, t, g = mid
+    # a short window keeps the scan mode (windows cubed per hub root) cheap
+    roots = torch.from_numpy(synth.root_sample(25, len(src), 32)).cuda()
+    tr = tmotif.Tree(NESTED_STARS, 120)
+    a = tmotif.count(g, tr, roots=roots, mode=D)
+    b = tmotif.count(g, tr, roots=roots, mode=D | tmotif.TM_LEAF_SCAN)
+    split = torch.full((32,), 64, dtype=torch.int32, device="cuda")
+    c = tmotif.count(g, tr, roots=roots, mode=tmotif.TM_SCHED_PLANNED, root_split=split)
+    assert a.tolist() == b.tolist() == c.tolist()
