@@ -296,18 +296,33 @@ def run_serving(args):
     for i in range(4):
         tk = srv.submit(*qs[i])
         srv.poll(tk, wait=True)
-    tickets = []
-    start = time.perf_counter()
-    with ClockSampler(local_rank) as clk:
-        for i, q in enumerate(qs):
-            now = time.perf_counter() - start
-            if arrivals[i] > now:
-                time.sleep(arrivals[i] - now)
+
+    def phase(arr, queries):
+        tickets = []
+        t_start = time.perf_counter()
+        for i, q in enumerate(queries):
+            now = time.perf_counter() - t_start
+            if arr[i] > now:
+                time.sleep(arr[i] - now)
             tickets.append(srv.submit(*q))
-        print("submitted %d requests in %.1f s" % (len(tickets), time.perf_counter() - start), file=sys.stderr,
+        print("submitted %d requests in %.1f s" % (len(tickets), time.perf_counter() - t_start), file=sys.stderr,
               flush=True)
-        res = [srv.poll(tk, wait=True) for tk in tickets]
-        end = time.perf_counter()
+        out = [srv.poll(tk, wait=True) for tk in tickets]
+        return out, time.perf_counter() - t_start
+
+    with ClockSampler(local_rank) as clk:
+        res, wall = phase(arrivals, qs)
+    stress = None
+    if args.stress_rate > 0:
+        n_s = int(args.stress_rate * args.stress_duration)
+        arr_s = np.cumsum(rng.exponential(1.0 / args.stress_rate, n_s))
+        qs_s = [synth.serving_query(90_000 + i, len(src), args.query_roots) for i in range(n_s)]
+        res_s, wall_s = phase(arr_s, qs_s)
+        lat_s = np.array([st["latency_ms"] for _, st in res_s])
+        stress = {"rate": args.stress_rate, "requests": n_s, "qps": n_s / wall_s,
+                  "p50_ms": float(np.percentile(lat_s, 50)), "p99_ms": float(np.percentile(lat_s, 99)),
+                  "mean_batch": float(np.mean([st["batch_size"] for _, st in res_s])),
+                  "root_edges_per_s": sum(len(q[0]) * len(q[2]) for q in qs_s) / wall_s}
     info = srv.info()
     srv.close()
     lat = np.array([st["latency_ms"] for _, st in res])
@@ -318,7 +333,6 @@ def run_serving(args):
         alone = tmotif.count(g, tmotif.Tree(ms_, d), roots=r, mode=tmotif.TM_SCHED_DYNAMIC)
         if res[i][0].tolist() != alone.tolist():
             raise SystemExit("served counts differ from the request counted alone")
-    wall = end - start
     units = sum(len(q[0]) * len(q[2]) for q in qs)
     line = {
         "metric": "serving: p99 request latency (ms) under Poisson arrivals, continuous batching",
@@ -326,7 +340,7 @@ def run_serving(args):
         "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
         "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
         "mean_ms": float(lat.mean()), "qps": n_req / wall, "root_edges_per_s": units / wall,
-        "mean_batch": float(sizes.mean()), "max_batch_seen": int(sizes.max()), "server": info,
+        "mean_batch": float(sizes.mean()), "max_batch_seen": int(sizes.max()), "server": info, "stress": stress,
         "config": {"workload": "%s: %d nodes, %d edges, Zipf(%.1f), bursty; %d requests at %.0f/s (Poisson); "
                                "each 1-16 motifs of 2-5 edges, window log-uniform in [60, 86400] s, %d sampled roots"
                                % (spec.name, spec.n_nodes, spec.n_edges, spec.zipf_s, n_req, rate, args.query_roots),
@@ -401,6 +415,8 @@ def main():
     ap.add_argument("--max-batch", type=int, default=32)
     ap.add_argument("--mem-budget", type=int, default=4 << 30)
     ap.add_argument("--serving-small", action="store_true")
+    ap.add_argument("--stress-rate", type=float, default=2000.0)
+    ap.add_argument("--stress-duration", type=float, default=5.0)
     ap.add_argument("--mode", type=int, default=0, help="extra tm_count mode bits")
     args = ap.parse_args()
     if args.impl == "reference":

@@ -284,6 +284,24 @@ def root_sample(seed: int, n_edges: int, n_roots: int) -> np.ndarray:
     return np.sort(pick).astype(np.int32)
 
 
+def root_sample_sparse(seed: int, n_edges: int, n_roots: int) -> np.ndarray:
+    """A seeded uniform sample of distinct root eids for n_roots << n_edges,
+    ascending: indices floor(u * n_edges) in draw order, duplicates skipped."""
+    if n_roots * 64 > n_edges:
+        return root_sample(seed, n_edges, n_roots)
+    out, seen, pos = [], set(), 0
+    while len(out) < n_roots:
+        u = rand_uniform(seed, 15, pos, 2 * n_roots)
+        pos += 2 * n_roots
+        for x in (u * n_edges).astype(np.int64):
+            if int(x) not in seen:
+                seen.add(int(x))
+                out.append(int(x))
+                if len(out) == n_roots:
+                    break
+    return np.sort(np.array(out, np.int32))
+
+
 # ----------------------------------------------------------------------------
 # workload configurations
 # ----------------------------------------------------------------------------
@@ -335,7 +353,7 @@ def serving_query(seed: int, n_edges: int, n_roots: int = 64):
     ms = query_motifs(seed, hi_edges=5)
     u = rand_uniform(seed, 14, 0, 1)[0]
     delta = int(math.exp(math.log(60) + u * (math.log(86400) - math.log(60))))
-    return ms, delta, root_sample(seed, n_edges, n_roots)
+    return ms, delta, root_sample_sparse(seed, n_edges, n_roots)
 
 
 def batched_sets(n_sets: int = 64, base_seed: int = 1000):

@@ -285,3 +285,11 @@ def test_tree_is_radix_trie(seed):
 def test_canonical_labels():
     assert mgtree.canonical([(5, 3), (3, 9), (9, 5)]) == ((0, 1), (1, 2), (2, 0))
     assert mgtree.canonical([(2, 1), (0, 1)]) == ((0, 1), (2, 1))
+
+
+def test_sparse_root_sample_is_distinct_sorted_and_seeded():
+    a = synth.root_sample_sparse(5, 10**9, 500)
+    b = synth.root_sample_sparse(5, 10**9, 500)
+    assert np.array_equal(a, b) and len(set(a.tolist())) == 500
+    assert np.all(np.diff(a) > 0) and a.min() >= 0 and a.max() < 10**9
+    assert not np.array_equal(a, synth.root_sample_sparse(6, 10**9, 500))
