@@ -33,6 +33,7 @@ WORKLOADS = {
     "mid": ("MID", "CONFIG2_MOTIFS", 3600, 64),
     "tiny": ("TINY", "CONFIG1_MOTIFS", 10_000, 50_000),
     "batched": (None, None, None, 65536),
+    "probe": (None, None, None, 4),
     "serving": (None, None, None, 64),
 }
 
@@ -353,6 +354,25 @@ def run_serving(args):
     return 0
 
 
+def run_probe(args):
+    """One co-mining launch on the mid workload's first --roots sampled roots
+    (default 4): the small case the kernel profiles are taken on."""
+    import torch
+    from paper_2507_14813_b300 import build, synth, tmotif
+    build.build()
+    src, dst, t = synth.make_graph(synth.MID)
+    g = tmotif.Graph(src, dst, t, synth.MID.n_nodes, presorted=True)
+    tr = tmotif.Tree(synth.CONFIG2_MOTIFS, synth.MID_DELTA)
+    r = torch.from_numpy(synth.root_sample(100, len(src), 64)[:args.roots or 4]).cuda()
+    out = torch.zeros(len(synth.CONFIG2_MOTIFS), dtype=torch.int64, device="cuda")
+    t0 = time.perf_counter()
+    tmotif.tm_count(g.h, tr.h, roots=r, counts=out, mode=tmotif.TM_SCHED_DYNAMIC)
+    torch.cuda.synchronize()
+    print(json.dumps({"probe": "mid, %d roots" % len(r), "counts": out.cpu().tolist(),
+                      "seconds": time.perf_counter() - t0}))
+    return 0
+
+
 def run_reference(args):
     rank, local_rank, world = env_rank()
     if rank != 0:
@@ -421,6 +441,8 @@ def main():
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "probe":
+        return run_probe(args)
     if args.workload == "batched":
         return run_batched(args)
     if args.workload == "serving":

@@ -471,7 +471,7 @@ struct Miner {
         }
         if (complete && N.n_par > 0) {
             for (int ci = 0; ci < N.n_par; ci++) {
-                const DevNode L = p.tr.nodes[N.child_begin + N.n_seq + ci];
+                const DevNode &L = p.tr.nodes[N.child_begin + N.n_seq + ci];
                 if (!(L.qmask & rmask)) continue;
                 uint32_t S2 = __ballot_sync(0xffffffffu, c.y < min(ws.ehi[L.dmax], cap)) & S;
                 if (S2) leaf_batch(L, k, S2, uk, vk, cs, cd, c.y, frame_hi(N), suf, c.x, peers, S);
@@ -594,7 +594,7 @@ struct Miner {
     // its list with edge ids in (eid[k-1], ehi].
     __device__ void open(int k, int node, int sib_end) {
         cache_release(k);                               // a sibling re-opening this level
-        const DevNode N = p.tr.nodes[node];
+        const DevNode &N = p.tr.nodes[node];
         if (!(N.qmask & rmask)) {                       // no query of this root below this node
             set_frame(k, node, sib_end, kListGlobal, 0, 0, 0, false, 0, false, 0);
             return;
@@ -799,23 +799,34 @@ struct Miner {
 
     __device__ __forceinline__ int32_t frame_hi(const DevNode &N) const { return min(ws.ehi[N.dmax], cap); }
 
-    // Load and filter the next chunk of level k.
-    __device__ void load_chunk(int k) {
-        const DevNode N = p.tr.nodes[ws.node[k]];
-        const int8_t lt = ws.ltype[k];
-        const bool down = ws.star[k];                   // star frames run from the top
-        const int64_t end = ws.end[k];
-        const int64_t base = down ? max(ws.pos[k], end - 32) : ws.pos[k];
+    // First position of level k's next chunk (star frames run from the top).
+    __device__ __forceinline__ int64_t chunk_base(int k) const {
+        return ws.star[k] ? max(ws.pos[k], ws.end[k] - 32) : ws.pos[k];
+    }
+
+    // This lane's entry of the chunk of level k starting at `base` (lists end at `end`).
+    __device__ __forceinline__ int2 fetch(int8_t lt, int64_t base, int64_t end) const {
         const int64_t i = base + lane;
-        const int32_t last = ws.eid[k - 1];
-        const int32_t hi = frame_hi(N);
-        bool valid = i < end;
         int2 c = make_int2(0, 0);
-        if (valid) {
+        if (i < end) {
             if (lt == kListOut) c = __ldg(&p.g.out_adj[i]);
             else if (lt == kListIn) c = __ldg(&p.g.in_adj[i]);
             else c = make_int2(0, (int32_t)i);
         }
+        return c;
+    }
+
+    // Filter the chunk of level k at `base` (entries c, valid below `end`):
+    // advance the frame, count and evaluate its survivors, keep those to
+    // descend in mask[k].
+    __device__ void step(int k, int64_t base, int64_t end, int2 c) {
+        const DevNode &N = p.tr.nodes[ws.node[k]];
+        const int8_t lt = ws.ltype[k];
+        const bool down = ws.star[k];                   // star frames run from the top
+        const int64_t i = base + lane;
+        const int32_t last = ws.eid[k - 1];
+        const int32_t hi = frame_hi(N);
+        bool valid = i < end;
         const bool inwin = c.y <= hi;
         const uint32_t outw = __ballot_sync(0xffffffffu, valid && !inwin);
         valid = valid && inwin && c.y > last;
@@ -846,10 +857,10 @@ struct Miner {
         if (lane == 0) {
             ws.cbase[k] = base;
             if (down) {
-                ws.end[k] = base;
+                ws.end[k] = min(ws.end[k], base);
                 ws.suf[k] = suf + __popc(S);
             } else {
-                ws.pos[k] = outw ? end : base + 32;
+                ws.pos[k] = outw ? ws.end[k] : max(ws.pos[k], base + 32);
             }
         }
         uint32_t D = survivors(k, N, S, c, suf);
@@ -858,6 +869,48 @@ struct Miner {
         __syncwarp();
         if (lane == 0) ws.mask[k] = D;
         __syncwarp();
+    }
+
+    // Load and filter the next chunk of level k.
+    __device__ void load_chunk(int k) {
+        const int64_t base = chunk_base(k);
+        const int64_t end = ws.end[k];
+        step(k, base, end, fetch(ws.ltype[k], base, end));
+    }
+
+    // A level whose survivors are only counted (nothing to descend): run all
+    // its chunks, fetching the next chunk before filtering the current one.
+    __device__ void drain(int k, int kbase) {
+        const int8_t lt = ws.ltype[k];
+        int64_t base = chunk_base(k);
+        int64_t end = ws.end[k];
+        int2 c = fetch(lt, base, end);
+        while (true) {
+            // claim the current chunk so a donation cannot hand it out
+            __syncwarp();
+            if (lane == 0) {
+                if (ws.star[k]) ws.end[k] = base;
+                else ws.pos[k] = base + 32;
+            }
+            __syncwarp();
+            if (p.react && ++polls >= p.poll_every) {
+                polls = 0;
+                maybe_donate(kbase, k);
+            }
+            const bool more = ws.pos[k] < ws.end[k];
+            int64_t nbase = 0, nend = 0;
+            int2 nc = make_int2(0, 0);
+            if (more) {
+                nbase = chunk_base(k);
+                nend = ws.end[k];
+                nc = fetch(lt, nbase, nend);
+            }
+            step(k, base, end, c);
+            if (!more || ws.pos[k] >= ws.end[k]) break;   // done, or the window ended in this chunk
+            base = nbase;
+            end = nend;
+            c = nc;
+        }
     }
 
     // Depth-first walk of the frames from level `kbase` up.
@@ -869,7 +922,7 @@ struct Miner {
             if (m) {
                 const int j = __ffs(m) - 1;
                 const int2 cj = ws.cand[k][j];
-                const DevNode N = p.tr.nodes[ws.node[k]];
+                const DevNode &N = p.tr.nodes[ws.node[k]];
                 const int8_t lt = ws.ltype[k];
                 int32_t cs, cd;
                 if (lt == kListOut) { cs = ws.lvert[k]; cd = cj.x; }
@@ -896,6 +949,10 @@ struct Miner {
                 continue;
             }
             if (ws.pos[k] < ws.end[k]) {
+                if (!ws.seq[k]) {                        // counted only: pipelined
+                    drain(k, kbase);
+                    continue;
+                }
                 if (p.react && ++polls >= p.poll_every) {
                     polls = 0;
                     maybe_donate(kbase, k);
@@ -919,7 +976,7 @@ struct Miner {
         if (a == b) return;                             // injective map needs a != b
         windows(r);
         if (lane == 0) ws.cache_owner = -1;
-        const DevNode N0 = p.tr.nodes[0];
+        const DevNode &N0 = p.tr.nodes[0];
         set_frame(0, 0, 1, kListGlobal, -1, 0, 0, seq_of(N0, 0), 0, false, 0);
         if (lane == 0) ws.cbase[0] = r;
         // level 0: the root edge as a one-candidate chunk on lane 0
@@ -938,7 +995,7 @@ struct Miner {
         const DevGraph &g = p.g;
         const int k = tk.k;
         windows(tk.eid[0]);
-        const DevNode N = p.tr.nodes[tk.node];
+        const DevNode &N = p.tr.nodes[tk.node];
         if (lane == 0) {
             for (int i = 0; i < k; i++) {
                 const int32_t e = tk.eid[i];
