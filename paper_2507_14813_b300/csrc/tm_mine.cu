@@ -48,6 +48,12 @@ constexpr int kThreads = kWarps * 32;
 constexpr int kSmemCounters = 2048;       // per-CTA counters kept in shared memory up to this many
 constexpr int kLaneScanMax = 24;          // leaf windows up to this size are scanned by the lane
 constexpr uint32_t kCacheEmpty = 0xffffffffu;
+constexpr int kSlots = 256;               // occurrence-table slots per warp
+constexpr int kSlotShift = 24;            // 32 - log2(kSlots)
+// star frames: later entries with the same far end come from ...
+enum : int8_t { kSameGallop = 0,          // ... the pair run (galloping search)
+                kSameTable = 1,           // ... the frame's occurrence table (pair run when the slot is taken)
+                kSameChunk = 2 };         // ... the chunk itself (the whole window is one chunk)
 
 constexpr int kQueueCap = 1 << 20;        // tasks per launch (slots are not reused)
 constexpr int kPollEvery = 4;             // default: chunk loads between looks at the idle counter
@@ -124,8 +130,9 @@ struct WarpState {
     int8_t star[kMaxE];       // star leaves are counted from level k: scanned top-down, suf[k] kept
     int64_t wend[kMaxE];      // end of level k's window (a donated slice may end earlier)
     int64_t suf[kMaxE];       // star frames: survivors of level k above the scan cursor, up to wend
-    uint32_t ckey[64];        // later-occurrence counts per candidate endpoint, for one star frame
-    uint32_t cval[64];
+    int8_t same_mode[kMaxE];  // star frames: how later same-endpoint entries are found (kSame*)
+    uint32_t ckey[kSlots];    // later-occurrence counts per candidate endpoint, for one star frame
+    uint32_t cval[kSlots];
     int32_t cache_owner;      // level whose star frame owns ckey/cval, or -1
     int32_t m2g[kMaxV];
     int32_t ehi[TM_MAX_DELTAS];
@@ -136,6 +143,8 @@ struct Work {
 };
 
 __device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long x) {
+    // 32 values below 2^27 sum below 2^32: one reduction instruction
+    if (__all_sync(0xffffffffu, x < (1ull << 27))) return __reduce_add_sync(0xffffffffu, (unsigned)x);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
     return x;
@@ -327,10 +336,12 @@ struct Miner {
     int polls;                         // chunk loads since the last look at the idle counter
     int split_h;                       // planned slices for the current root's first-level lists
     uint64_t rmask;                    // queries served by the current root
+    unsigned long long acc;            // this lane's deferred star-leaf count (drain of one frame)
+    int32_t acc_ref;                   // ref index whose counts are deferred, or -1
     int32_t cap;                       // last edge id any of those queries' windows reaches
 
     __device__ Miner(const Params &pp, WarpState &s, unsigned long long *c, int l)
-        : p(pp), ws(s), s_cnt(c), lane(l), polls(0), split_h(0), rmask(~0ull), cap(INT32_MAX) {
+        : p(pp), ws(s), s_cnt(c), lane(l), polls(0), split_h(0), rmask(~0ull), acc(0), acc_ref(-1), cap(INT32_MAX) {
         for (int i = 0; i < kStatFields; i++) w.v[i] = 0;
     }
 
@@ -423,9 +434,16 @@ struct Miner {
                     unsigned long long pr = 0;
                     const int64_t later = suf + __popc(Sall & above);
                     int64_t same;
-                    const uint32_t slot = ((uint32_t)y * 2654435761u) >> 26;
-                    if (ws.cache_owner == k && ws.ckey[slot] == (uint32_t)y) {
+                    const int8_t sm = ws.same_mode[k];
+                    const uint32_t slot = ((uint32_t)y * 2654435761u) >> kSlotShift;
+                    const uint32_t key = sm == kSameTable ? ws.ckey[slot] : 0u;
+                    if (sm == kSameChunk) {
+                        same = __popc(peers & above);
+                    } else if (sm == kSameTable && key == (uint32_t)y) {
                         same = (int64_t)ws.cval[slot] + __popc(peers & above);
+                    } else if (sm == kSameTable && key == kCacheEmpty) {
+                        // a value seen above would have claimed this empty slot
+                        same = __popc(peers & above);
                     } else {
                         same = run_tail(p.g.pair_eid, __ldg(p.g.pr_pos + last), __ldg(p.g.pr_end + last), hi, pr);
                         pr += 2;
@@ -439,6 +457,10 @@ struct Miner {
                     c = (unsigned long long)leaf_count(L, k + 1, uk, vk, cs, cd, last, hi);
                 }
             }
+            if (L.ref_begin + i == acc_ref) {           // summed once when the frame is drained
+                acc += c;
+                continue;
+            }
             c = warp_sum_u64(c);
             if (lane == 0) add_count(ref.counter, c);
         }
@@ -447,9 +469,8 @@ struct Miner {
     // Chunk-level work for survivors S of level k of node N: count the refs
     // of a completed node, count single-edge leaves lane-parallel; returns
     // the survivors to descend.
-    __device__ uint32_t survivors(int k, const DevNode &N, uint32_t S, int2 c, int64_t suf) {
+    __device__ uint32_t survivors(int k, const DevNode &N, uint32_t S, int2 c, int64_t suf, uint32_t peers) {
         if (S == 0) return 0;
-        const uint32_t peers = ws.star[k] ? __match_any_sync(0xffffffffu, ((S >> lane) & 1u) ? c.x : -1) : 0u;
         const int uk = N.eu[k], vk = N.ev[k];
         int32_t cs, cd;
         const int8_t lt = ws.ltype[k];
@@ -536,8 +557,8 @@ struct Miner {
     __device__ void cache_claim(int k) {
         if (ws.cache_owner >= 0) return;
         __syncwarp();
-        ws.ckey[lane] = kCacheEmpty;
-        ws.ckey[lane + 32] = kCacheEmpty;
+#pragma unroll
+        for (int i = 0; i < kSlots / 32; i++) ws.ckey[lane + 32 * i] = kCacheEmpty;
         if (lane == 0) ws.cache_owner = k;
         __syncwarp();
     }
@@ -552,7 +573,7 @@ struct Miner {
     __device__ void cache_add(uint32_t S, int32_t y, uint32_t peers) {
         if ((S >> lane) & 1u) {
             if (lane == __ffs(peers) - 1) {
-                const uint32_t slot = ((uint32_t)y * 2654435761u) >> 26;
+                const uint32_t slot = ((uint32_t)y * 2654435761u) >> kSlotShift;
                 const uint32_t key = ws.ckey[slot];
                 const uint32_t n = (uint32_t)__popc(peers);
                 if (key == (uint32_t)y) ws.cval[slot] += n;
@@ -621,7 +642,13 @@ struct Miner {
         }
         const bool star = lt != kListGlobal && star_of(N, k);
         set_frame(k, node, sib_end, lt, x, start, end, seq_of(N, k), end, star, 0);
-        if (star) cache_claim(k);
+        if (star) {
+            int8_t sm = kSameGallop;
+            if (end - start <= 32) sm = kSameChunk;      // every later entry is in this one chunk
+            else if (ws.cache_owner < 0) { cache_claim(k); sm = kSameTable; }
+            if (lane == 0) ws.same_mode[k] = sm;
+            __syncwarp();
+        }
         if (kStats && lane == 0) w.v[kStExp]++;
         if (k == 1 && split_h > 1) force_split(k, split_h);
     }
@@ -863,9 +890,9 @@ struct Miner {
                 ws.pos[k] = outw ? ws.end[k] : max(ws.pos[k], base + 32);
             }
         }
-        uint32_t D = survivors(k, N, S, c, suf);
-        if (down && ws.cache_owner == k)
-            cache_add(S, c.x, __match_any_sync(0xffffffffu, ((S >> lane) & 1u) ? c.x : -1));
+        const uint32_t peers = down ? __match_any_sync(0xffffffffu, ((S >> lane) & 1u) ? c.x : -1) : 0u;
+        uint32_t D = survivors(k, N, S, c, suf, peers);
+        if (down && ws.cache_owner == k) cache_add(S, c.x, peers);
         __syncwarp();
         if (lane == 0) ws.mask[k] = D;
         __syncwarp();
@@ -885,6 +912,17 @@ struct Miner {
         int64_t base = chunk_base(k);
         int64_t end = ws.end[k];
         int2 c = fetch(lt, base, end);
+        // a star frame counting one star leaf with one ref: sum that ref's
+        // counts in registers across chunks and add them once
+        const DevNode &N = p.tr.nodes[ws.node[k]];
+        acc = 0;
+        acc_ref = -1;
+        if (ws.star[k]) {
+            const DevNode *Ls = nullptr;
+            if ((N.flags & kNodeParLeaf) && k == N.k_end - 2) Ls = &N;
+            else if (k == N.k_end - 1 && N.n_par == 1) Ls = &p.tr.nodes[N.child_begin + N.n_seq];
+            if (Ls && (Ls->flags & kNodeStarLeaf) && Ls->n_ref == 1) acc_ref = Ls->ref_begin;
+        }
         while (true) {
             // claim the current chunk so a donation cannot hand it out
             __syncwarp();
@@ -910,6 +948,12 @@ struct Miner {
             base = nbase;
             end = nend;
             c = nc;
+        }
+        if (acc_ref >= 0) {
+            const unsigned long long tot = warp_sum_u64(acc);
+            if (lane == 0) add_count(p.tr.refs[acc_ref].counter, tot);
+            acc_ref = -1;
+            acc = 0;
         }
     }
 
@@ -949,7 +993,7 @@ struct Miner {
                 continue;
             }
             if (ws.pos[k] < ws.end[k]) {
-                if (!ws.seq[k]) {                        // counted only: pipelined
+                if (!ws.seq[k] && ws.end[k] - ws.pos[k] > 32) {   // counted only, several chunks: pipelined
                     drain(k, kbase);
                     continue;
                 }
@@ -983,7 +1027,7 @@ struct Miner {
         int2 c = make_int2(lane == 0 ? b : 0, lane == 0 ? r : 0);
         ws.cand[0][lane] = c;
         __syncwarp();
-        uint32_t D = survivors(0, N0, 1u, c, 0);
+        uint32_t D = survivors(0, N0, 1u, c, 0, 0u);
         __syncwarp();
         if (lane == 0) ws.mask[0] = D;
         __syncwarp();
@@ -1015,6 +1059,8 @@ struct Miner {
         // a top-down slice needs the survivors above it, up to the window's end
         const int64_t suf = star ? count_survivors(N, k, lt, tk.hi, tk.wend, true) : 0;
         set_frame(k, tk.node, tk.node + 1, lt, x, tk.lo, tk.hi, seq_of(N, k), tk.wend, star, suf);
+        if (lane == 0) ws.same_mode[k] = kSameTable;
+        __syncwarp();
         run(k);
     }
 };
@@ -1102,6 +1148,20 @@ __global__ void k_status(const QueueHdr *q, int n_launch, int32_t *status) {
     *status = e;
 }
 
+// Static shared memory plus up to kSmemCounters per-CTA counters exceeds the
+// default 48 KiB per block; allow the larger dynamic part once per device.
+int allow_counter_smem() {
+    static int done[64] = {0};
+    int dev = 0;
+    TM_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev >= 0 && dev < 64 && done[dev]) return TM_OK;
+    const int bytes = (int)(sizeof(unsigned long long) * kSmemCounters);
+    TM_CUDA_TRY(cudaFuncSetAttribute(k_mine<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+    TM_CUDA_TRY(cudaFuncSetAttribute(k_mine<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+    if (dev >= 0 && dev < 64) done[dev] = 1;
+    return TM_OK;
+}
+
 // Everything a count needs besides its inputs: where the scratch lives and
 // how the launches are shaped.
 struct Plan {
@@ -1160,6 +1220,7 @@ int make_plan(const tm_graph *g, const tm_tree *tr, const tm_count_args *args, b
     TM_CUDA_TRY(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev));
     P->smem_cnt = P->n_motifs <= kSmemCounters;
     P->dyn_smem = P->smem_cnt ? (int)(sizeof(unsigned long long) * P->n_motifs) : 0;
+    TM_TRY(allow_counter_smem());
     int per_sm = 0;
     TM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, stats ? k_mine<true> : k_mine<false>,
                                                               kThreads, P->dyn_smem));
@@ -1609,6 +1670,7 @@ extern "C" int tm_count_noalloc(const tm_graph *g, const tm_tree *tr, const int3
         int n_sm = 0, per_sm = 0;
         TM_CUDA_TRY(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev));
         const int dyn_smem = (int)(sizeof(unsigned long long) * n_motifs);
+        TM_TRY(allow_counter_smem());
         TM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_mine<false>, kThreads, dyn_smem));
         per_sm = std::max(per_sm, 1);
         const int blocks = n_sm * per_sm;
