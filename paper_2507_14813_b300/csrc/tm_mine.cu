@@ -1080,7 +1080,10 @@ __device__ void flush_work(Miner<kStats> &M, const Work &before, const Params &p
 }
 
 template <bool kStats>
-__global__ void __launch_bounds__(kThreads, 4) k_mine(Params p) {
+#ifndef TM_MIN_BLOCKS
+#define TM_MIN_BLOCKS 4   // CTAs per SM the register budget is sized for (64 registers per thread)
+#endif
+__global__ void __launch_bounds__(kThreads, TM_MIN_BLOCKS) k_mine(Params p) {
     extern __shared__ unsigned long long s_cnt[];
     __shared__ WarpState s_ws[kWarps];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;

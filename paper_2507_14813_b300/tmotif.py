@@ -15,7 +15,7 @@ from typing import Optional, Sequence
 import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libtmotif.so")
+LIB_PATH = os.environ.get("TMOTIF_LIB") or os.path.join(HERE, "libtmotif.so")
 
 TM_OK = 0
 TM_EINVAL = -1
