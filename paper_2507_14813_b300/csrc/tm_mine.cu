@@ -46,8 +46,10 @@ namespace {
 constexpr int kWarps = 8;                 // warps per CTA
 constexpr int kThreads = kWarps * 32;
 constexpr int kSmemCounters = 2048;       // per-CTA counters kept in shared memory up to this many
+constexpr int kWarpCounters = kSmemCounters / kWarps;  // up to this many: one private slice per warp
 constexpr int kLaneScanMax = 24;          // leaf windows up to this size are scanned by the lane
 constexpr uint32_t kCacheEmpty = 0xffffffffu;
+constexpr unsigned long long kSlotEmpty = (unsigned long long)kCacheEmpty << 32;
 constexpr int kSlots = 256;               // occurrence-table slots per warp
 constexpr int kSlotShift = 24;            // 32 - log2(kSlots)
 // star frames: later entries with the same far end come from ...
@@ -101,7 +103,7 @@ struct Params {
     int *ready;                       // kQueueCap publish flags, zeroed (dynamic mode)
     unsigned long long *stats;        // kStatFields totals or null
     int32_t chunk;                    // roots claimed per cursor step
-    int32_t smem_counters;            // 1: per-CTA counters in shared memory
+    int32_t smem_counters;            // 1: per-CTA counters in shared memory, 2: one slice per warp
     int32_t dynamic;                  // 1: persistent launch with a task queue
     int32_t react;                    // 1: warps donate slices when others are idle
     const int32_t *split;             // per root index: slices for its first-level lists, or null
@@ -131,9 +133,10 @@ struct WarpState {
     int64_t wend[kMaxE];      // end of level k's window (a donated slice may end earlier)
     int64_t suf[kMaxE];       // star frames: survivors of level k above the scan cursor, up to wend
     int8_t same_mode[kMaxE];  // star frames: how later same-endpoint entries are found (kSame*)
-    uint32_t ckey[kSlots];    // later-occurrence counts per candidate endpoint, for one star frame
-    uint32_t cval[kSlots];
-    int32_t cache_owner;      // level whose star frame owns ckey/cval, or -1
+    // later-occurrence counts per candidate endpoint, for one star frame:
+    // (endpoint << 32) | survivors with that endpoint scanned so far
+    unsigned long long cslot[kSlots];
+    int32_t cache_owner;      // level whose star frame owns cslot, or -1
     int32_t m2g[kMaxV];
     int32_t ehi[TM_MAX_DELTAS];
 };
@@ -339,16 +342,19 @@ struct Miner {
     unsigned long long acc;            // this lane's deferred star-leaf count (drain of one frame)
     int32_t acc_ref;                   // ref index whose counts are deferred, or -1
     int32_t cap;                       // last edge id any of those queries' windows reaches
+    int32_t gsame;                     // star frames: this lane's later same-endpoint survivors, or -1
 
     __device__ Miner(const Params &pp, WarpState &s, unsigned long long *c, int l)
-        : p(pp), ws(s), s_cnt(c), lane(l), polls(0), split_h(0), rmask(~0ull), acc(0), acc_ref(-1), cap(INT32_MAX) {
+        : p(pp), ws(s), s_cnt(c), lane(l), polls(0), split_h(0), rmask(~0ull), acc(0), acc_ref(-1), cap(INT32_MAX),
+          gsame(-1) {
         for (int i = 0; i < kStatFields; i++) w.v[i] = 0;
     }
 
     __device__ __forceinline__ void add_count(int32_t counter, unsigned long long c) {
         // called by one lane
         if (c == 0) return;
-        if (p.smem_counters) atomicAdd(&s_cnt[counter], c);
+        if (p.smem_counters == 2) s_cnt[counter] += c;          // the warp's own slice
+        else if (p.smem_counters) atomicAdd(&s_cnt[counter], c);
         else atomicAdd(&p.counts[counter], c);
         if (p.per_root_counts)
             atomicAdd((unsigned long long *)&p.per_root_counts[ri * p.tr.n_counters + counter], c);
@@ -436,11 +442,12 @@ struct Miner {
                     int64_t same;
                     const int8_t sm = ws.same_mode[k];
                     const uint32_t slot = ((uint32_t)y * 2654435761u) >> kSlotShift;
-                    const uint32_t key = sm == kSameTable ? ws.ckey[slot] : 0u;
+                    const unsigned long long ent = sm == kSameTable ? ws.cslot[slot] : 0ull;
+                    const uint32_t key = (uint32_t)(ent >> 32);
                     if (sm == kSameChunk) {
                         same = __popc(peers & above);
                     } else if (sm == kSameTable && key == (uint32_t)y) {
-                        same = (int64_t)ws.cval[slot] + __popc(peers & above);
+                        same = (int64_t)(uint32_t)ent + __popc(peers & above);
                     } else if (sm == kSameTable && key == kCacheEmpty) {
                         // a value seen above would have claimed this empty slot
                         same = __popc(peers & above);
@@ -449,6 +456,7 @@ struct Miner {
                         pr += 2;
                     }
                     c = (unsigned long long)(later - same);
+                    gsame = (int32_t)same;
                     if (kStats) {
                         w.v[kStPairProbe] += pr;
                         w.v[kStLeaf] += 1;
@@ -558,7 +566,7 @@ struct Miner {
         if (ws.cache_owner >= 0) return;
         __syncwarp();
 #pragma unroll
-        for (int i = 0; i < kSlots / 32; i++) ws.ckey[lane + 32 * i] = kCacheEmpty;
+        for (int i = 0; i < kSlots / 32; i++) ws.cslot[lane + 32 * i] = kSlotEmpty;
         if (lane == 0) ws.cache_owner = k;
         __syncwarp();
     }
@@ -569,16 +577,30 @@ struct Miner {
         __syncwarp();
     }
 
-    // Add the survivors of one chunk (groups of equal endpoint `peers`) to the table.
-    __device__ void cache_add(uint32_t S, int32_t y, uint32_t peers) {
-        if ((S >> lane) & 1u) {
-            if (lane == __ffs(peers) - 1) {
-                const uint32_t slot = ((uint32_t)y * 2654435761u) >> kSlotShift;
-                const uint32_t key = ws.ckey[slot];
-                const uint32_t n = (uint32_t)__popc(peers);
-                if (key == (uint32_t)y) ws.cval[slot] += n;
-                else if (key == kCacheEmpty && atomicCAS(&ws.ckey[slot], kCacheEmpty, (uint32_t)y) == kCacheEmpty)
-                    ws.cval[slot] = n;
+    // Add the survivors of one chunk (groups of equal endpoint `peers`) to the
+    // table.  `known`: for the lowest survivor of a group, its later survivors
+    // with the same endpoint (exact), or -1.  A slot held by another endpoint
+    // goes to the group's endpoint when its count so far (known + 1) is larger:
+    // the hot endpoints keep their slots.  Every slot update is one
+    // compare-and-swap of the whole (endpoint, count) word, so a count is
+    // never added to an endpoint it was not taken for.
+    __device__ void cache_add(uint32_t S, int32_t y, uint32_t peers, int32_t known) {
+        if (((S >> lane) & 1u) && lane == __ffs(peers) - 1) {
+            const uint32_t slot = ((uint32_t)y * 2654435761u) >> kSlotShift;
+            const unsigned long long n = (unsigned long long)__popc(peers);
+            unsigned long long e = ws.cslot[slot];
+            while (true) {
+                const uint32_t key = (uint32_t)(e >> 32);
+                unsigned long long v;
+                if (key == (uint32_t)y) v = e + n;
+                // an empty slot: y was not seen above (it would have claimed the slot)
+                else if (key == kCacheEmpty) v = ((unsigned long long)(uint32_t)y << 32) | n;
+                else if (known >= 0 && (unsigned long long)known + 1 > (e & 0xffffffffull))
+                    v = ((unsigned long long)(uint32_t)y << 32) | (unsigned long long)(known + 1);
+                else break;
+                const unsigned long long o = atomicCAS(&ws.cslot[slot], e, v);
+                if (o == e) break;
+                e = o;
             }
         }
         __syncwarp();
@@ -605,7 +627,7 @@ struct Miner {
             }
             const uint32_t S = __ballot_sync(0xffffffffu, ok);
             n += __popc(S);
-            if (fill) cache_add(S, c.x, __match_any_sync(0xffffffffu, ok ? c.x : -1));
+            if (fill) cache_add(S, c.x, __match_any_sync(0xffffffffu, ok ? c.x : -1), -1);
             if (kStats && lane == 0) w.v[kStCand] += (unsigned long long)((wend - b) < 32 ? (wend - b) : 32);
         }
         return n;
@@ -891,8 +913,9 @@ struct Miner {
             }
         }
         const uint32_t peers = down ? __match_any_sync(0xffffffffu, ((S >> lane) & 1u) ? c.x : -1) : 0u;
+        gsame = -1;
         uint32_t D = survivors(k, N, S, c, suf, peers);
-        if (down && ws.cache_owner == k) cache_add(S, c.x, peers);
+        if (down && ws.cache_owner == k) cache_add(S, c.x, peers, gsame);
         __syncwarp();
         if (lane == 0) ws.mask[k] = D;
         __syncwarp();
@@ -1081,16 +1104,17 @@ __device__ void flush_work(Miner<kStats> &M, const Work &before, const Params &p
 
 template <bool kStats>
 #ifndef TM_MIN_BLOCKS
-#define TM_MIN_BLOCKS 4   // CTAs per SM the register budget is sized for (64 registers per thread)
+#define TM_MIN_BLOCKS 3   // CTAs per SM the register budget is sized for (80 registers per thread)
 #endif
 __global__ void __launch_bounds__(kThreads, TM_MIN_BLOCKS) k_mine(Params p) {
     extern __shared__ unsigned long long s_cnt[];
     __shared__ WarpState s_ws[kWarps];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (p.smem_counters)
-        for (int i = threadIdx.x; i < p.tr.n_counters; i += blockDim.x) s_cnt[i] = 0;
+    const int n_cnt = p.tr.n_counters;
+    const int n_smem = p.smem_counters == 2 ? kWarps * n_cnt : (p.smem_counters ? n_cnt : 0);
+    for (int i = threadIdx.x; i < n_smem; i += blockDim.x) s_cnt[i] = 0;
     __syncthreads();
-    Miner<kStats> M(p, s_ws[warp], s_cnt, lane);
+    Miner<kStats> M(p, s_ws[warp], s_cnt + (p.smem_counters == 2 ? warp * n_cnt : 0), lane);
     if (p.dynamic && lane == 0) atomicAdd(&p.q->busy, 1);
     while (true) {
         if (p.dynamic) {
@@ -1132,8 +1156,12 @@ __global__ void __launch_bounds__(kThreads, TM_MIN_BLOCKS) k_mine(Params p) {
     }
     __syncthreads();
     if (p.smem_counters)
-        for (int i = threadIdx.x; i < p.tr.n_counters; i += blockDim.x)
-            if (s_cnt[i]) atomicAdd(&p.counts[i], s_cnt[i]);
+        for (int i = threadIdx.x; i < n_cnt; i += blockDim.x) {
+            unsigned long long c = s_cnt[i];
+            if (p.smem_counters == 2)
+                for (int wi = 1; wi < kWarps; wi++) c += s_cnt[wi * n_cnt + i];
+            if (c) atomicAdd(&p.counts[i], c);
+        }
 }
 
 __global__ void k_to_i64(const unsigned long long *a, int64_t *b, int n) {
@@ -1174,7 +1202,7 @@ struct Plan {
     const int32_t *roots = nullptr;     // device
     const uint64_t *root_qmask = nullptr; // device, serving batches only
     int blocks = 0, dyn_smem = 0;
-    bool smem_cnt = true;
+    bool smem_cnt = true, warp_cnt = true;
     int32_t chunk = 1;
     int poll_every = kPollEvery, donate_seq = kDonateSeq, donate_leaf = kDonateLeaf;
     size_t o_q = 0, o_tasks = 0, o_ready = 0, bytes = 0, b_ready = 0;
@@ -1222,7 +1250,8 @@ int make_plan(const tm_graph *g, const tm_tree *tr, const tm_count_args *args, b
     TM_CUDA_TRY(cudaGetDevice(&dev));
     TM_CUDA_TRY(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev));
     P->smem_cnt = P->n_motifs <= kSmemCounters;
-    P->dyn_smem = P->smem_cnt ? (int)(sizeof(unsigned long long) * P->n_motifs) : 0;
+    P->warp_cnt = P->n_motifs <= kWarpCounters;
+    P->dyn_smem = (int)(sizeof(unsigned long long) * P->n_motifs) * (P->warp_cnt ? kWarps : P->smem_cnt ? 1 : 0);
     TM_TRY(allow_counter_smem());
     int per_sm = 0;
     TM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, stats ? k_mine<true> : k_mine<false>,
@@ -1259,7 +1288,7 @@ int enqueue(const tm_graph *g, const tm_tree *tr, const tm_count_args *args, con
         if (given) dt = *given;
         else TM_TRY(tree_device(tr, P.comine ? 0 : 1 + L, P.par, s, &dt));
         if (P.dynamic) TM_CUDA_TRY(cudaMemsetAsync(d_ready, 0, P.b_ready, s));
-        Params prm;
+        Params prm{};                 // every field not set below is zero
         prm.g = g->d;
         prm.tr = dt;
         prm.roots = P.roots;
@@ -1273,7 +1302,7 @@ int enqueue(const tm_graph *g, const tm_tree *tr, const tm_count_args *args, con
         prm.ready = d_ready;
         prm.stats = d_st;
         prm.chunk = P.chunk;
-        prm.smem_counters = P.smem_cnt ? 1 : 0;
+        prm.smem_counters = P.warp_cnt ? 2 : P.smem_cnt ? 1 : 0;
         prm.dynamic = P.dynamic ? 1 : 0;
         prm.react = P.react ? 1 : 0;
         prm.split = P.planned ? args->root_split : nullptr;
@@ -1677,7 +1706,7 @@ extern "C" int tm_count_noalloc(const tm_graph *g, const tm_tree *tr, const int3
         TM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_mine<false>, kThreads, dyn_smem));
         per_sm = std::max(per_sm, 1);
         const int blocks = n_sm * per_sm;
-        Params prm;
+        Params prm{};                 // every field not set below is zero
         prm.g = g->d;
         prm.tr = image_tree(img, b + kNoAllocTree);
         prm.roots = roots;
