@@ -134,6 +134,7 @@ int tm_tree_free(tm_tree *tr);
 /* mode bits */
 #define TM_COMINE 0x0u        /* walk the MG-Tree (Algorithm 3) */
 #define TM_PERMOTIF 0x1u      /* one chain per distinct motif, one launch each (Algorithm 1) */
+#define TM_AUTO 0x2u          /* TM_COMINE or TM_PERMOTIF, as tm_comine_advice decides */
 #define TM_LEAF_SCAN 0x10u    /* count a leaf's last edge by scanning its window only */
 #define TM_SCHED_DYNAMIC 0x100u /* persistent launch, heavy subtrees split across warps */
 #define TM_SCHED_PLANNED 0x200u /* persistent launch; cut root i's first-level lists into root_split[i] slices */
@@ -150,7 +151,7 @@ int tm_tree_free(tm_tree *tr);
 #define TM_WORK_FIELDS 4
 
 typedef struct {
-    uint32_t mode;            /* TM_COMINE or TM_PERMOTIF, | TM_LEAF_SCAN, | TM_SCHED_DYNAMIC */
+    uint32_t mode;            /* TM_COMINE, TM_PERMOTIF or TM_AUTO, | TM_LEAF_SCAN, | TM_SCHED_* */
     uint32_t flags;           /* TM_ROOTS_DEVICE, TM_COUNTS_DEVICE */
     const int32_t *roots;     /* root edge ids (any order, may repeat); NULL: range below */
     int64_t n_roots;
@@ -197,6 +198,35 @@ typedef struct {
  */
 int tm_count(const tm_graph *g, const tm_tree *tr, const tm_count_args *args, int64_t *counts,
              tm_run_stats *stats, void *stream);
+
+/* ------------------------------------------------------------ co-mining decision */
+/*
+ * Whether the undirected view of the graph is bipartite.  Section 6 found
+ * co-mining faster on bipartite data graphs in every experiment: matches
+ * cannot join two vertices of one side, so shared prefixes are pruned early.
+ * Computed on the device once per graph and cached in the handle (connected
+ * components of the bipartite double cover by label hooking and pointer
+ * jumping; bipartite iff no vertex is in the component of its own copy).
+ * A graph with a self-loop is not bipartite; a graph without edges is.
+ *   out: 1 bipartite, 0 not.  Synchronises `stream` on first use.
+ * Errors: TM_EINVAL (NULL argument), TM_ENOMEM (2 x n_nodes int32 labels),
+ * TM_EUNSUPPORTED (n_nodes >= 2^30), TM_ECUDA.
+ */
+int tm_graph_bipartite(const tm_graph *g, int32_t *out, void *stream);
+
+/* Below this similarity metric (SM, tm_tree_info.similarity) per-motif
+ * mining beat co-mining on the GPU in Section 6. */
+#define TM_COMINE_MIN_SM 0.44
+
+/*
+ * The co-mining decision of Section 6 ("Heuristic for Co-Mining"): co-mine on
+ * a bipartite graph; otherwise co-mine iff the tree's SM >= TM_COMINE_MIN_SM.
+ * (The paper's remaining advice, to prefer a smaller window, is the caller's
+ * choice of delta.)  tm_count with TM_AUTO applies it.
+ *   out: 1 co-mine (TM_COMINE), 0 mine each motif alone (TM_PERMOTIF).
+ * Errors: as tm_graph_bipartite.
+ */
+int tm_comine_advice(const tm_graph *g, const tm_tree *tr, int32_t *out, void *stream);
 
 /* ------------------------------------------------------------ serving */
 /*

@@ -1,6 +1,6 @@
 // C-ABI entry points (include/tmotif.h): argument checks, handle lifetime,
-// error reporting.  The work itself is in tm_graph.cu, tm_tree.cpp and
-// tm_mine.cu.
+// error reporting.  The work itself is in tm_graph.cu, tm_tree.cpp,
+// tm_mine.cu and tm_heur.cu.
 #include <cuda_runtime.h>
 
 #include <cstring>
@@ -115,13 +115,36 @@ int tm_count(const tm_graph *g, const tm_tree *tr, const tm_count_args *args, in
              void *stream) {
     g_last_error.clear();
     if (!g || !tr || !args || !counts) { set_error("tm_count: NULL argument"); return TM_EINVAL; }
-    if (args->mode & ~(TM_PERMOTIF | TM_LEAF_SCAN | TM_SCHED_DYNAMIC | TM_SCHED_PLANNED)) {
+    if (args->mode & ~(TM_PERMOTIF | TM_AUTO | TM_LEAF_SCAN | TM_SCHED_DYNAMIC | TM_SCHED_PLANNED)) {
         set_error("tm_count: unknown mode bit");
+        return TM_EINVAL;
+    }
+    if ((args->mode & TM_AUTO) && (args->mode & TM_PERMOTIF)) {
+        set_error("tm_count: TM_AUTO and TM_PERMOTIF together");
         return TM_EINVAL;
     }
     if (args->flags & ~(TM_ROOTS_DEVICE | TM_COUNTS_DEVICE)) { set_error("tm_count: unknown flag"); return TM_EINVAL; }
     if (args->roots && args->n_roots < 0) { set_error("tm_count: n_roots < 0"); return TM_EINVAL; }
+    if (args->mode & TM_AUTO) {
+        int32_t co = 1;
+        TM_TRY(comine_advice(g, tr, (cudaStream_t)stream, &co));
+        tm_count_args a = *args;
+        a.mode = (a.mode & ~TM_AUTO) | (co ? TM_COMINE : TM_PERMOTIF);
+        return mine(g, tr, &a, counts, stats, (cudaStream_t)stream);
+    }
     return mine(g, tr, args, counts, stats, (cudaStream_t)stream);
+}
+
+int tm_graph_bipartite(const tm_graph *g, int32_t *out, void *stream) {
+    g_last_error.clear();
+    if (!g || !out) { set_error("tm_graph_bipartite: NULL argument"); return TM_EINVAL; }
+    return graph_bipartite(g, (cudaStream_t)stream, out);
+}
+
+int tm_comine_advice(const tm_graph *g, const tm_tree *tr, int32_t *out, void *stream) {
+    g_last_error.clear();
+    if (!g || !tr || !out) { set_error("tm_comine_advice: NULL argument"); return TM_EINVAL; }
+    return comine_advice(g, tr, (cudaStream_t)stream, out);
 }
 
 }  // extern "C"

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -74,6 +75,8 @@ struct tm_graph {
     int64_t max_out = 0, max_in = 0;
     int64_t bytes = 0;
     int device = 0;
+    mutable std::mutex heur_mutex;    // guards the cached analysis below
+    mutable int32_t bipartite = -1;   // undirected view bipartite (1), not (0), unknown (-1)
 };
 
 namespace tmo {
@@ -190,6 +193,11 @@ void tree_release(tm_tree *tr);
 int tree_device(const tm_tree *tr, int which, bool par_leaves, cudaStream_t s, DevTree *out);
 
 // mining (tm_mine.cu)
+// tm_heur.cu: bipartiteness of the undirected view (cached in the handle) and
+// the co-mining decision built on it
+int graph_bipartite(const tm_graph *g, cudaStream_t s, int32_t *out);
+int comine_advice(const tm_graph *g, const tm_tree *tr, cudaStream_t s, int32_t *out);
+
 int mine(const tm_graph *g, const tm_tree *tr, const tm_count_args *args, int64_t *counts,
          tm_run_stats *stats, cudaStream_t s);
 // a serving batch: MG-Tree already on the device (dt), roots with query masks;

@@ -31,6 +31,8 @@ TM_PRESORTED = 0x2
 
 TM_COMINE = 0x0
 TM_PERMOTIF = 0x1
+TM_AUTO = 0x2
+TM_COMINE_MIN_SM = 0.44
 TM_LEAF_SCAN = 0x10
 TM_SCHED_DYNAMIC = 0x100
 TM_SCHED_PLANNED = 0x200
@@ -117,6 +119,7 @@ _lib = None
 
 EXPORTS = ("tm_graph_load", "tm_graph_get_info", "tm_graph_edges", "tm_graph_free", "tm_tree_build",
            "tm_tree_get_info", "tm_tree_get_node", "tm_tree_free", "tm_count", "tm_count_noalloc",
+           "tm_graph_bipartite", "tm_comine_advice",
            "tm_features", "tm_model_create", "tm_model_free", "tm_model_get_params", "tm_model_set_params",
            "tm_model_fit_norm", "tm_model_predict", "tm_model_loss_grad", "tm_model_train", "tm_plan",
            "tm_exec_create", "tm_exec_launch", "tm_exec_status", "tm_exec_free", "tm_autotune",
@@ -243,6 +246,19 @@ def tm_graph_edges(g):
 
 def tm_graph_free(g) -> None:
     _check(lib().tm_graph_free(g))
+
+
+def tm_graph_bipartite(g, stream=None) -> bool:
+    out = ctypes.c_int32(-1)
+    _check(lib().tm_graph_bipartite(g, ctypes.byref(out), _stream(stream)))
+    return bool(out.value)
+
+
+def tm_comine_advice(g, tr, stream=None) -> bool:
+    """True: co-mine (TM_COMINE); False: mine each motif alone (TM_PERMOTIF)."""
+    out = ctypes.c_int32(-1)
+    _check(lib().tm_comine_advice(g, tr, ctypes.byref(out), _stream(stream)))
+    return bool(out.value)
 
 
 def motif_arrays(motifs: Sequence):
@@ -541,6 +557,9 @@ class Graph:
 
     def edges(self):
         return tm_graph_edges(self.h)
+
+    def bipartite(self) -> bool:
+        return tm_graph_bipartite(self.h)
 
     def close(self):
         if getattr(self, "h", None) is not None and _lib is not None:
