@@ -199,6 +199,32 @@ typedef struct {
 int tm_count(const tm_graph *g, const tm_tree *tr, const tm_count_args *args, int64_t *counts,
              tm_run_stats *stats, void *stream);
 
+/* ------------------------------------------------------------ enumeration */
+/* One match: the motif (index into the caller's motif list) and the ids of the
+ * edges matched to its edges, in the motif's edge order (so ascending). */
+typedef struct {
+    int32_t motif;
+    int32_t n_edges;          /* edges of that motif */
+    int32_t eid[TM_MAX_EDGES]; /* -1 past n_edges */
+} tm_match;
+
+/*
+ * Enumerate the matches that tm_count counts.  Algorithm 1 records each match
+ * it completes; the paper's experiments only count (reading 13).  Every match
+ * of every motif of `tr` whose first edge is a selected root (args->roots /
+ * n_roots or root_lo / root_hi, as tm_count; args->mode must not hold
+ * TM_PERMOTIF, TM_AUTO or TM_LEAF_SCAN, scheduling bits are ignored) is
+ * written to `out`, in no particular order, until `cap` records are written.
+ *   out:     device memory, cap records, caller-owned (may be NULL if cap == 0)
+ *   n_found: host; the number of matches, which exceeds cap when records were
+ *            dropped (then which cap matches were written is unspecified)
+ *   counts:  optional host int64[n_motifs]: matches per motif (= tm_count)
+ * Synchronises `stream`.  Errors: TM_EINVAL (NULL handle, out NULL with
+ * cap > 0, cap < 0, bad mode, root out of range), TM_ENOMEM, TM_ECUDA.
+ */
+int tm_enumerate(const tm_graph *g, const tm_tree *tr, const tm_count_args *args, tm_match *out, int64_t cap,
+                 int64_t *n_found, int64_t *counts, void *stream);
+
 /* ------------------------------------------------------------ co-mining decision */
 /*
  * Whether the undirected view of the graph is bipartite.  Section 6 found

@@ -1,6 +1,6 @@
 // C-ABI entry points (include/tmotif.h): argument checks, handle lifetime,
 // error reporting.  The work itself is in tm_graph.cu, tm_tree.cpp,
-// tm_mine.cu and tm_heur.cu.
+// tm_mine.cu, tm_heur.cu and tm_enum.cu.
 #include <cuda_runtime.h>
 
 #include <cstring>
@@ -133,6 +133,22 @@ int tm_count(const tm_graph *g, const tm_tree *tr, const tm_count_args *args, in
         return mine(g, tr, &a, counts, stats, (cudaStream_t)stream);
     }
     return mine(g, tr, args, counts, stats, (cudaStream_t)stream);
+}
+
+int tm_enumerate(const tm_graph *g, const tm_tree *tr, const tm_count_args *args, tm_match *out, int64_t cap,
+                 int64_t *n_found, int64_t *counts, void *stream) {
+    g_last_error.clear();
+    if (!g || !tr || !args || !n_found) { set_error("tm_enumerate: NULL argument"); return TM_EINVAL; }
+    if (cap < 0 || (cap > 0 && !out)) { set_error("tm_enumerate: out must hold cap >= 0 records"); return TM_EINVAL; }
+    if (args->mode & (TM_PERMOTIF | TM_AUTO | TM_LEAF_SCAN)) {
+        set_error("tm_enumerate: enumeration walks the MG-Tree (no TM_PERMOTIF, TM_AUTO, TM_LEAF_SCAN)");
+        return TM_EINVAL;
+    }
+    if (args->mode & ~(TM_SCHED_DYNAMIC | TM_SCHED_PLANNED)) { set_error("tm_enumerate: unknown mode bit"); return TM_EINVAL; }
+    if (args->flags & ~(TM_ROOTS_DEVICE | TM_COUNTS_DEVICE)) { set_error("tm_enumerate: unknown flag"); return TM_EINVAL; }
+    if (args->roots && args->n_roots < 0) { set_error("tm_enumerate: n_roots < 0"); return TM_EINVAL; }
+    *n_found = 0;
+    return enumerate(g, tr, args, out, cap, n_found, counts, (cudaStream_t)stream);
 }
 
 int tm_graph_bipartite(const tm_graph *g, int32_t *out, void *stream) {

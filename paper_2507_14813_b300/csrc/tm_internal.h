@@ -192,12 +192,16 @@ void tree_release(tm_tree *tr);
 // device copy of tree `which` (0 = MG-Tree, 1 + i = chain i), uploaded on first use
 int tree_device(const tm_tree *tr, int which, bool par_leaves, cudaStream_t s, DevTree *out);
 
-// mining (tm_mine.cu)
 // tm_heur.cu: bipartiteness of the undirected view (cached in the handle) and
 // the co-mining decision built on it
 int graph_bipartite(const tm_graph *g, cudaStream_t s, int32_t *out);
 int comine_advice(const tm_graph *g, const tm_tree *tr, cudaStream_t s, int32_t *out);
 
+// tm_enum.cu: every match written to a bounded device buffer
+int enumerate(const tm_graph *g, const tm_tree *tr, const tm_count_args *args, tm_match *out, int64_t cap,
+              int64_t *n_found, int64_t *counts, cudaStream_t s);
+
+// mining (tm_mine.cu)
 int mine(const tm_graph *g, const tm_tree *tr, const tm_count_args *args, int64_t *counts,
          tm_run_stats *stats, cudaStream_t s);
 // a serving batch: MG-Tree already on the device (dt), roots with query masks;

@@ -119,7 +119,7 @@ _lib = None
 
 EXPORTS = ("tm_graph_load", "tm_graph_get_info", "tm_graph_edges", "tm_graph_free", "tm_tree_build",
            "tm_tree_get_info", "tm_tree_get_node", "tm_tree_free", "tm_count", "tm_count_noalloc",
-           "tm_graph_bipartite", "tm_comine_advice",
+           "tm_graph_bipartite", "tm_comine_advice", "tm_enumerate",
            "tm_features", "tm_model_create", "tm_model_free", "tm_model_get_params", "tm_model_set_params",
            "tm_model_fit_norm", "tm_model_predict", "tm_model_loss_grad", "tm_model_train", "tm_plan",
            "tm_exec_create", "tm_exec_launch", "tm_exec_status", "tm_exec_free", "tm_autotune",
@@ -354,6 +354,32 @@ def tm_count(g, tr, mode: int = TM_COMINE, roots=None, root_lo: int = 0, root_hi
     st = tm_run_stats()
     _check(lib().tm_count(g, tr, ctypes.byref(a), pc, ctypes.byref(st) if stats else None, _stream(stream)))
     return (out, st.as_dict()) if stats else out
+
+
+MATCH_FIELDS = 2 + TM_MAX_EDGES        # tm_match: motif, n_edges, eid[TM_MAX_EDGES] (int32 each)
+
+
+def tm_enumerate(g, tr, cap: int, roots=None, root_lo: int = 0, root_hi: int = 0, mode: int = TM_COMINE,
+                 stream=None):
+    """Every match of every motif with its first edge among the roots.
+
+    Returns ``(matches, n_found, counts)``: ``matches`` an int32 array of
+    shape (min(n_found, cap), 2 + TM_MAX_EDGES) with rows (motif, n_edges,
+    eid_1, ..., eid_8; -1 past n_edges), ``n_found`` the number of matches
+    (> cap when records were dropped) and ``counts`` the matches per motif.
+    """
+    import torch
+    a, keep = _count_args(mode, roots, root_lo, root_hi)
+    n_motifs = tm_tree_get_info(tr)["n_motifs"]
+    buf = torch.empty((max(cap, 0), MATCH_FIELDS), dtype=torch.int32, device="cuda") if cap > 0 else None
+    out_p = ctypes.c_void_p(buf.data_ptr()) if buf is not None else None
+    n_found = ctypes.c_int64(0)
+    counts = np.zeros(n_motifs, np.int64)
+    _check(lib().tm_enumerate(g, tr, ctypes.byref(a), out_p, ctypes.c_int64(cap), ctypes.byref(n_found),
+                              counts.ctypes.data_as(ctypes.c_void_p), _stream(stream)))
+    n = min(n_found.value, max(cap, 0))
+    matches = buf[:n].cpu().numpy() if buf is not None else np.zeros((0, MATCH_FIELDS), np.int32)
+    return matches, n_found.value, counts
 
 
 def tm_count_noalloc(g, tr, counts, roots=None, root_lo: int = 0, root_hi: int = 0, stream=None):

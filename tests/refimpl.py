@@ -39,6 +39,28 @@ def brute_force(src, dst, t, motif, delta):
     return cnt
 
 
+def brute_force_matches(src, dst, t, motif, delta):
+    """The matches themselves: every k-tuple of edge ids e_1 < ... < e_k within
+    the window that has an injective map (the same test as brute_force)."""
+    E = len(src)
+    k = len(motif)
+    out = []
+    for tup in itertools.combinations(range(E), k):
+        if t[tup[-1]] - t[tup[0]] > delta:
+            continue
+        f = {}
+        ok = True
+        for (mu, mv), e in zip(motif, tup):
+            for mx, gx in ((mu, int(src[e])), (mv, int(dst[e]))):
+                if f.setdefault(mx, gx) != gx:
+                    ok = False
+            if not ok:
+                break
+        if ok and len(set(f.values())) == len(f):
+            out.append(tup)
+    return out
+
+
 def window_end(t, delta):
     """For each edge e: the last edge id with t <= t[e] + delta."""
     return np.searchsorted(t, t + delta, side="right") - 1
