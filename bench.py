@@ -116,12 +116,12 @@ class ClockSampler:
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one timed mining
 # launch of the default benchmark, from an ncu capture of that launch, keyed by
 # a hash of the kernel source it was taken on; any other source reports null.
-# b5e5b5c1766a922c: mean of the three timed launches of
+# 40f3baa3fc7c70a3: mean of the three timed launches of
 #   ncu --metrics gpu__time_duration.sum,dram__bytes_read.sum,dram__bytes_write.sum
 #       --clock-control none -c 400 python bench.py --steps 3 --warmup 3
 #       --no-cpu-baseline --no-e2e --no-permotif --no-learned
-# (467.7 MB read + 64.7 MB written).
-TRAFFIC = {"b5e5b5c1766a922c": 532.4e6}
+# (475.9 MB read + 65.5 MB written).
+TRAFFIC = {"40f3baa3fc7c70a3": 541.4e6}
 
 
 def kernel_hash():
@@ -283,7 +283,7 @@ def run_batched(args):
                    "l2": "flushed between steps (256 MiB write)", "launch": "CUDA graph replay of one persistent launch"},
         "tree": tr.info(), "autotune": tune, "sets_one_by_one_ms": seq_ms,
         "batched_speedup_vs_one_by_one": (seq_ms / ms) if seq_ms else None,
-        "work": {k: st[k] for k in ("candidates", "probes", "leaf_evals", "tasks_split", "algo_bytes")},
+        "work": {k: st[k] for k in ("candidates", "probes", "leaf_evals", "tasks_split", "algo_bytes", "warp_imbalance")},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": None},
         "gpu_launches": 3 * args.steps, "clocks": clk.summary(),
@@ -693,7 +693,7 @@ def main():
         "counts": ref_counts.cpu().tolist(),
         "permotif_ms_per_step": perm,
         "comine_speedup_vs_permotif": (perm / ms_step) if perm else None,
-        "work": {k: st[k] for k in ("candidates", "expansions", "probes", "leaf_evals", "algo_bytes")},
+        "work": {k: st[k] for k in ("candidates", "expansions", "probes", "leaf_evals", "algo_bytes", "warp_imbalance")},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak,
                      "traffic": TRAFFIC.get(kernel_hash()) if args.workload == "mid" and len(roots) == 64 else None,

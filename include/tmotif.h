@@ -179,6 +179,8 @@ typedef struct {
     int64_t tasks_split;      /* subtrees handed to other warps (TM_SCHED_DYNAMIC) */
     int64_t launches;         /* kernel launches issued by the call */
     double kernel_ms;         /* device time of the mining launches */
+    double warp_imbalance;    /* max / mean over warps of busy cycles (time not spent waiting
+                                 for work) in the stats launch: 1 is perfect balance */
 } tm_run_stats;
 
 /*

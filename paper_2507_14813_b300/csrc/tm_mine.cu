@@ -101,7 +101,7 @@ struct Params {
     QueueHdr *q;                      // zeroed before launch
     Task *tasks;                      // kQueueCap (dynamic mode)
     int *ready;                       // kQueueCap publish flags, zeroed (dynamic mode)
-    unsigned long long *stats;        // kStatFields totals or null
+    unsigned long long *stats;        // kStatFields totals, then kBusyFields, or null
     int32_t chunk;                    // roots claimed per cursor step
     int32_t smem_counters;            // 1: per-CTA counters in shared memory, 2: one slice per warp
     int32_t dynamic;                  // 1: persistent launch with a task queue
@@ -115,6 +115,8 @@ struct Params {
 };
 
 enum { kStCand = 0, kStExp, kStListProbe, kStHashProbe, kStPairProbe, kStLeaf, kStRoots, kStSplit, kStatFields };
+// after the kStatFields totals: busy cycles of the busiest warp, their sum, and the warps
+enum { kBusyMax = 0, kBusySum, kBusyWarps, kBusyFields };
 
 struct WarpState {
     int2 cand[kMaxE][32];
@@ -1116,10 +1118,16 @@ __global__ void __launch_bounds__(kThreads, TM_MIN_BLOCKS) k_mine(Params p) {
     __syncthreads();
     Miner<kStats> M(p, s_ws[warp], s_cnt + (p.smem_counters == 2 ? warp * n_cnt : 0), lane);
     if (p.dynamic && lane == 0) atomicAdd(&p.q->busy, 1);
+    // stats launch: this warp's cycles spent other than waiting for work
+    const long long t_begin = kStats ? clock64() : 0;
+    long long idle = 0;
     while (true) {
         if (p.dynamic) {
             Task tk;
-            if (M.pop(tk)) {
+            const long long tp = kStats ? clock64() : 0;
+            const bool got = M.pop(tk);
+            if (kStats && !got) idle += clock64() - tp;
+            if (got) {
                 M.ri = tk.ri;
                 M.split_h = 0;
                 M.rmask = p.root_qmask ? __ldg(p.root_qmask + tk.ri) : ~0ull;
@@ -1146,7 +1154,17 @@ __global__ void __launch_bounds__(kThreads, TM_MIN_BLOCKS) k_mine(Params p) {
             }
             continue;
         }
-        if (!p.dynamic || !M.wait_for_work()) break;
+        if (!p.dynamic) break;
+        const long long tw = kStats ? clock64() : 0;
+        const bool more = M.wait_for_work();
+        if (kStats) idle += clock64() - tw;
+        if (!more) break;
+    }
+    if (kStats && lane == 0) {
+        const unsigned long long busy = (unsigned long long)max(0ll, clock64() - t_begin - idle);
+        atomicMax(&p.stats[kStatFields + kBusyMax], busy);
+        atomicAdd(&p.stats[kStatFields + kBusySum], busy);
+        atomicAdd(&p.stats[kStatFields + kBusyWarps], 1ull);
     }
     if (kStats) {
         for (int f = 0; f < kStatFields; f++) {
@@ -1237,7 +1255,7 @@ int make_plan(const tm_graph *g, const tm_tree *tr, const tm_count_args *args, b
     if (args->donate_seq > 0) P->donate_seq = args->donate_seq;
     if (args->donate_leaf > 0) P->donate_leaf = args->donate_leaf;
     P->n_launch = P->comine ? 1 : (int)tr->chains.size();
-    const size_t b_cnt = sizeof(unsigned long long) * (size_t)(P->n_motifs + kStatFields);
+    const size_t b_cnt = sizeof(unsigned long long) * (size_t)(P->n_motifs + kStatFields + kBusyFields);
     P->o_q = (b_cnt + 255) / 256 * 256;
     const size_t b_q = sizeof(QueueHdr) * (size_t)P->n_launch;
     P->o_tasks = (P->o_q + b_q + 255) / 256 * 256;
@@ -1436,7 +1454,7 @@ int mine(const tm_graph *g, const tm_tree *tr, const tm_count_args *args, int64_
         for (int i = 0; i < P.n_motifs; i++) counts[i] = (int64_t)h[i];
     }
     if (stats) {
-        unsigned long long hs[kStatFields];
+        unsigned long long hs[kStatFields + kBusyFields];
         cudaMemcpyAsync(hs, d_cnt + P.n_motifs, sizeof(hs), cudaMemcpyDeviceToHost, s);
         cudaError_t e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) {
@@ -1454,6 +1472,8 @@ int mine(const tm_graph *g, const tm_tree *tr, const tm_count_args *args, int64_
         stats->algo_bytes = (int64_t)(16 * hs[kStRoots] + 8 * hs[kStCand] + 8 * hs[kStListProbe] +
                                       16 * hs[kStHashProbe] + 4 * hs[kStPairProbe]);
         stats->tasks_split = (int64_t)hs[kStSplit];
+        const unsigned long long *hb = hs + kStatFields;
+        stats->warp_imbalance = hb[kBusySum] ? (double)hb[kBusyMax] * (double)hb[kBusyWarps] / (double)hb[kBusySum] : 0.0;
         stats->launches = launches;
         stats->kernel_ms = ms;
     }
