@@ -114,14 +114,16 @@ class ClockSampler:
 
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one timed mining
-# launch of the default benchmark, from an ncu capture of that launch, keyed by
-# a hash of the kernel source it was taken on; any other source reports null.
-# 40f3baa3fc7c70a3: mean of the three timed launches of
+# launch of the default benchmark, from a one-pass ncu capture of that launch,
+# keyed by a hash of the kernel source it was taken on and by the schedule of
+# the timed step; any other source reports null.  For 40f3baa3fc7c70a3, the
+# mean of the three timed launches of
 #   ncu --metrics gpu__time_duration.sum,dram__bytes_read.sum,dram__bytes_write.sum
-#       --clock-control none -c 400 python bench.py --steps 3 --warmup 3
-#       --no-cpu-baseline --no-e2e --no-permotif --no-learned
-# (475.9 MB read + 65.5 MB written).
-TRAFFIC = {"40f3baa3fc7c70a3": 541.4e6}
+#       --clock-control none -c 3000 python bench.py --steps 3 --warmup 3
+#       --no-cpu-baseline --no-e2e --no-permotif
+# (learned: 398.7 MB read + 40.1 MB written), and of the same command with
+# --no-learned and -c 400 (reactive: 475.9 MB read + 65.5 MB written).
+TRAFFIC = {"40f3baa3fc7c70a3": {"learned": 438.7e6, "reactive": 541.4e6}}
 
 
 def kernel_hash():
@@ -164,9 +166,25 @@ def cpu_baseline(src, dst, t, motifs, delta, roots, seconds=20.0, threads=1):
     return value, done_min
 
 
-def learned_schedule(args, tmotif, g, tr, src, rank, d_roots, counts, ref_counts, stream, flush, mode):
-    """Train the cost model on measured per-root work of a separate sample,
-    plan the benchmark's roots by it, and time the planned launch."""
+def plan_launches(n_roots):
+    """Kernels of one learned plan: k_features, then tm_plan's k_mlp_fwd,
+    k_plan_keys, four radix passes (k_rs_hist, the histogram scan, k_rs_scatter)
+    and k_plan_apply.  The histogram scan is one k_scan_tile while the 256
+    buckets x tiles fit one scan tile, else two more launches per level."""
+    tiles = max(1, -(-n_roots // 4096))
+    scan = 1
+    n = 256 * tiles
+    while n > 1024:                     # k_scan_tile + recursive scan + k_scan_add
+        scan += 2
+        n = -(-n // 1024)
+    return 1 + 2 + 4 * (2 + scan) + 1
+
+
+def train_cost_model(args, tmotif, g, tr, src, rank, d_roots):
+    """Train the cost model (a11) on measured per-root work of a separate root
+    sample, then judge its predictions on the benchmark's own roots against
+    their measured work.  Runs before any timed region: the trained model is
+    an input of the step, like the graph."""
     import torch
     from paper_2507_14813_b300 import synth
     n_train = args.train_roots
@@ -182,7 +200,6 @@ def learned_schedule(args, tmotif, g, tr, src, rank, d_roots, counts, ref_counts
     model.fit_norm(X)
     hist = model.train(X, y, epochs=120, batch=256, lr=3e-3)
     t_train = time.perf_counter() - t0
-    # prediction error on the benchmark's own roots, judged by their measured work
     R = len(d_roots)
     wr = torch.zeros((R, tmotif.TM_WORK_FIELDS), dtype=torch.int64, device="cuda")
     tmotif.tm_count(g.h, tr.h, roots=d_roots, per_root_work=wr, mode=tmotif.TM_SCHED_DYNAMIC, stats=True)
@@ -195,31 +212,10 @@ def learned_schedule(args, tmotif, g, tr, src, rank, d_roots, counts, ref_counts
     p = pb.cpu().numpy()
     rmse = float(np.sqrt(np.mean((p - yb) ** 2)))
     rank_corr = float(np.corrcoef(np.argsort(np.argsort(p)), np.argsort(np.argsort(yb)))[0, 1]) if R > 2 else None
-    ro = torch.zeros_like(d_roots)
-    sp = torch.zeros_like(d_roots)
-    model.plan(Xb, d_roots, ro, sp, unit_work=args.unit_work, max_split=args.max_split)
-    out = {}
-    for name, m in (("planned", tmotif.TM_SCHED_PLANNED), ("planned_dynamic", tmotif.TM_SCHED_PLANNED | tmotif.TM_SCHED_DYNAMIC)):
-        mm = (mode & ~tmotif.TM_SCHED_DYNAMIC) | m
-        tmotif.tm_count(g.h, tr.h, mode=mm, roots=ro, counts=counts, root_split=sp, stream=stream)
-        torch.cuda.synchronize()
-        if not torch.equal(counts, ref_counts):
-            raise SystemExit("planned counts differ")
-        ts = []
-        for i in range(max(1, min(args.steps, 3))):
-            flush.fill_(i & 0xFF)
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            tmotif.tm_count(g.h, tr.h, mode=mm, roots=ro, counts=counts, root_split=sp, stream=stream)
-            b.record(stream)
-            torch.cuda.synchronize()
-            ts.append(a.elapsed_time(b))
-        out[name + "_ms_per_step"] = statistics.median(ts)
-    out.update({"train_roots": n_train, "train_seconds": t_train, "final_train_loss": float(hist[-1]),
-                "label": "log1p(candidates + probes) per root", "rmse_log_work_on_bench_roots": rmse,
-                "spearman_on_bench_roots": rank_corr, "label_std_on_bench_roots": float(np.std(yb)),
-                "max_split": args.max_split, "unit_work": args.unit_work})
-    return out
+    return model, {"train_roots": n_train, "train_seconds": t_train, "final_train_loss": float(hist[-1]),
+                   "label": "log1p(candidates + probes) per root", "rmse_log_work_on_bench_roots": rmse,
+                   "spearman_on_bench_roots": rank_corr, "label_std_on_bench_roots": float(np.std(yb)),
+                   "max_split": args.max_split, "unit_work": args.unit_work}
 
 
 def run_batched(args):
@@ -610,17 +606,54 @@ def main():
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     mode = tmotif.TM_COMINE | args.mode | (0 if args.static else tmotif.TM_SCHED_DYNAMIC)
+    # learned scheduling (a11, a12): the model is trained before the timed
+    # region; every step computes features, predicts, plans and counts
+    model, learned = None, None
+    if not args.no_learned and not args.static:
+        model, learned = train_cost_model(args, tmotif, g, tr, src, rank, d_roots)
+    R = len(roots)
+    feats = torch.zeros((R, tmotif.TM_FEATURES), dtype=torch.float32, device="cuda")
+    ro = torch.zeros_like(d_roots)
+    sp = torch.zeros_like(d_roots)
 
-    def step(m):
-        tmotif.tm_count(g.h, tr.h, mode=m, roots=d_roots, counts=counts, stream=stream)
+    def plan(gh, th, r_dev, f, r_out, s_out):
+        tmotif.tm_features(gh, th, r_dev, f, stream=stream)
+        model.plan(f, r_dev, r_out, s_out, unit_work=args.unit_work, max_split=args.max_split, stream=stream)
 
+    def step(m, use_model):
+        if use_model:
+            plan(g.h, tr.h, d_roots, feats, ro, sp)
+            tmotif.tm_count(g.h, tr.h, mode=m | tmotif.TM_SCHED_PLANNED, roots=ro, counts=counts, root_split=sp,
+                            stream=stream)
+        else:
+            tmotif.tm_count(g.h, tr.h, mode=m, roots=d_roots, counts=counts, stream=stream)
+
+    def timed(m, use_model, n):
+        ts = []
+        for i in range(n):
+            flush.fill_(i & 0xFF)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            step(m, use_model)
+            b.record(stream)
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b))
+            if not torch.equal(counts, ref_counts):
+                raise SystemExit("counts differ between schedules or modes")
+        return statistics.median(ts)
+
+    use_model = model is not None
     for _ in range(args.warmup):
-        step(mode)
+        step(mode, use_model)
     torch.cuda.synchronize()
     ref_counts = counts.clone()
 
-    # stats of one untimed launch: algorithmic bytes and work counters
-    _, st = tmotif.tm_count(g.h, tr.h, mode=mode, roots=roots, stats=True, stream=stream)
+    # stats of one untimed launch of the same schedule: algorithmic bytes and work counters
+    if use_model:
+        _, st = tmotif.tm_count(g.h, tr.h, mode=mode | tmotif.TM_SCHED_PLANNED, roots=ro, root_split=sp,
+                                stats=True, stream=stream)
+    else:
+        _, st = tmotif.tm_count(g.h, tr.h, mode=mode, roots=roots, stats=True, stream=stream)
 
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     if world > 1:
@@ -630,7 +663,7 @@ def main():
         for i in range(args.steps):
             flush.fill_(i & 0xFF)
             ev[i][0].record(stream)
-            step(mode)
+            step(mode, use_model)
             ev[i][1].record(stream)
         torch.cuda.synchronize()
     if world > 1:
@@ -646,32 +679,23 @@ def main():
     ms_step = total_ms / args.steps
     units = len(roots) * n_m * world
     value = units / (ms_step / 1000.0)
+    n_cmp = max(1, min(args.steps, 3))
 
-    # per-motif comparator on the same roots (one chain tree per motif)
-    perm = None
+    # the same step without the model: reactive splitting alone
+    reactive = timed(mode, False, n_cmp) if use_model else None
+
+    # per-motif comparator on the same roots (one chain tree per motif), same schedule
+    perm = perm_reactive = None
     if not args.no_permotif:
-        step(mode | tmotif.TM_PERMOTIF)
+        step(mode | tmotif.TM_PERMOTIF, use_model)
         torch.cuda.synchronize()
         if not torch.equal(counts, ref_counts):
             raise SystemExit("per-motif counts differ from co-mined counts")
-        pm = []
-        for i in range(max(1, min(args.steps, 3))):
-            flush.fill_(i & 0xFF)
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            step(mode | tmotif.TM_PERMOTIF)
-            b.record(stream)
-            torch.cuda.synchronize()
-            pm.append(a.elapsed_time(b))
-        perm = statistics.median(pm)
+        perm = timed(mode | tmotif.TM_PERMOTIF, use_model, n_cmp)
+        if use_model:
+            perm_reactive = timed(mode | tmotif.TM_PERMOTIF, False, n_cmp)
 
-    # learned scheduling: a cost model trained on measured work of a separate
-    # root sample orders the benchmark's roots and cuts the heavy ones
-    learned = None
-    if not args.no_learned:
-        learned = learned_schedule(args, tmotif, g, tr, src, rank, d_roots, counts, ref_counts, stream, flush, mode)
-
-    # end to end through the C-ABI with host buffers: load, build, count, read back
+    # end to end through the C-ABI with host buffers: load, build, (plan,) count, read back
     e2e = None
     if not args.no_e2e:
         h_roots = roots.copy()
@@ -680,7 +704,14 @@ def main():
             t0 = time.perf_counter()
             g2 = tmotif.Graph(src, dst, t, spec.n_nodes, presorted=True)
             tr2 = tmotif.Tree(motifs, delta)
-            c2 = tmotif.tm_count(g2.h, tr2.h, mode=mode, roots=h_roots)
+            if use_model:
+                r2 = torch.from_numpy(h_roots).cuda()
+                f2 = torch.empty((R, tmotif.TM_FEATURES), dtype=torch.float32, device="cuda")
+                ro2, sp2 = torch.empty_like(r2), torch.empty_like(r2)
+                plan(g2.h, tr2.h, r2, f2, ro2, sp2)
+                c2 = tmotif.tm_count(g2.h, tr2.h, mode=mode | tmotif.TM_SCHED_PLANNED, roots=ro2, root_split=sp2)
+            else:
+                c2 = tmotif.tm_count(g2.h, tr2.h, mode=mode, roots=h_roots)
             g2.close()
             tr2.close()
             times.append(time.perf_counter() - t0)
@@ -702,19 +733,25 @@ def main():
         "roots_per_s": len(roots) * world / (ms_step / 1000.0),
         "counts_per_s": float(ref_counts.sum().item()) * world / (ms_step / 1000.0),
         "counts": ref_counts.cpu().tolist(),
+        "schedule": ("learned plan (features, MLP, sorted slices) + reactive splitting" if use_model
+                     else ("static, one warp per root" if args.static else "reactive splitting")),
+        "reactive_ms_per_step": reactive,
+        "learned_speedup_vs_reactive": (reactive / ms_step) if reactive else None,
         "permotif_ms_per_step": perm,
         "comine_speedup_vs_permotif": (perm / ms_step) if perm else None,
+        "permotif_reactive_ms_per_step": perm_reactive,
         "work": {k: st[k] for k in ("candidates", "expansions", "probes", "leaf_evals", "algo_bytes", "warp_imbalance")},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak,
-                     "traffic": TRAFFIC.get(kernel_hash()) if args.workload == "mid" and len(roots) == 64 else None,
+                     "traffic": (TRAFFIC.get(kernel_hash(), {}).get("learned" if use_model else "reactive")
+                                 if args.workload == "mid" and len(roots) == 64 and not args.static else None),
                      "kernel": "k_mine", "kernel_source": kernel_hash(),
                      "peak_kind": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else peak_kind},
-        "gpu_launches": 2 * args.steps,
+        "gpu_launches": (plan_launches(len(roots)) + 2 if use_model else 2) * args.steps,
         "clocks": clk.summary(),
     }
     if learned:
-        line["learned_schedule"] = learned
+        line["cost_model"] = learned
     if e2e:
         line["e2e"] = e2e
     if rank == 0 and not args.no_cpu_baseline:
