@@ -121,9 +121,10 @@ class ClockSampler:
 #   ncu --metrics gpu__time_duration.sum,dram__bytes_read.sum,dram__bytes_write.sum
 #       --clock-control none -c 3000 python bench.py --steps 3 --warmup 3
 #       --no-cpu-baseline --no-e2e --no-permotif
-# (learned: 398.7 MB read + 40.1 MB written), and of the same command with
-# --no-learned and -c 400 (reactive: 475.9 MB read + 65.5 MB written).
-TRAFFIC = {"40f3baa3fc7c70a3": {"learned": 438.7e6, "reactive": 541.4e6}}
+# (learned, unit_work 1e6, max_split 4096: 375.6 MB read + 39.1 MB written),
+# and of the same command with --no-learned and -c 400 (reactive: 475.9 MB read
+# + 65.5 MB written).
+TRAFFIC = {"40f3baa3fc7c70a3": {"learned": 414.8e6, "reactive": 541.4e6}}
 
 
 def kernel_hash():
@@ -562,8 +563,8 @@ def main():
     ap.add_argument("--static", action="store_true", help="one warp per root, no subtree splitting")
     ap.add_argument("--no-learned", action="store_true")
     ap.add_argument("--train-roots", type=int, default=512)
-    ap.add_argument("--unit-work", type=float, default=2e6)
-    ap.add_argument("--max-split", type=int, default=512)
+    ap.add_argument("--unit-work", type=float, default=1e6)
+    ap.add_argument("--max-split", type=int, default=4096)
     ap.add_argument("--rate", type=float, default=50.0)
     ap.add_argument("--duration", type=float, default=20.0)
     ap.add_argument("--query-roots", type=int, default=64)
