@@ -183,7 +183,7 @@ def plan_launches(n_roots):
 
 def train_cost_model(args, tmotif, g, tr, src, rank, d_roots):
     """Train the cost model (a11) on measured per-root work of a separate root
-    sample, then judge its predictions on the benchmark's own roots against
+    sample, then score its predictions on the benchmark's own roots against
     their measured work.  Runs before any timed region: the trained model is
     an input of the step, like the graph."""
     import torch
