@@ -121,10 +121,11 @@ class ClockSampler:
 #   ncu --metrics gpu__time_duration.sum,dram__bytes_read.sum,dram__bytes_write.sum
 #       --clock-control none -c 3000 python bench.py --steps 3 --warmup 3
 #       --no-cpu-baseline --no-e2e --no-permotif
-# (learned, unit_work 1e6, max_split 4096: 375.6 MB read + 39.1 MB written),
-# and of the same command with --no-learned and -c 400 (reactive: 475.9 MB read
-# + 65.5 MB written).
-TRAFFIC = {"40f3baa3fc7c70a3": {"learned": 414.8e6, "reactive": 541.4e6}}
+# with the default plan and tunables (unit_work 1e6, max_split 4096,
+# poll_every 16, donate_leaf 4096): learned, 369.97 MB read + 38.97 MB written;
+# reactive (the three comparison launches of the same run), 461.2 MB read +
+# 59.4 MB written.
+TRAFFIC = {"40f3baa3fc7c70a3": {"learned": 408.9e6, "reactive": 520.6e6}}
 
 
 def kernel_hash():
@@ -565,6 +566,9 @@ def main():
     ap.add_argument("--train-roots", type=int, default=512)
     ap.add_argument("--unit-work", type=float, default=1e6)
     ap.add_argument("--max-split", type=int, default=4096)
+    ap.add_argument("--poll-every", type=int, default=16, help="reactive splitting: chunk loads between polls")
+    ap.add_argument("--donate-leaf", type=int, default=4096,
+                    help="reactive splitting: shortest counting-only slice handed over")
     ap.add_argument("--rate", type=float, default=50.0)
     ap.add_argument("--duration", type=float, default=20.0)
     ap.add_argument("--query-roots", type=int, default=64)
@@ -621,13 +625,17 @@ def main():
         tmotif.tm_features(gh, th, r_dev, f, stream=stream)
         model.plan(f, r_dev, r_out, s_out, unit_work=args.unit_work, max_split=args.max_split, stream=stream)
 
+    # reactive-splitting tunables (chunk loads between looks for idle warps, the
+    # shortest counting-only slice worth handing over), from a sweep on this workload
+    tune = {"ctas_per_sm": 0, "donate_seq": 0, "donate_leaf": args.donate_leaf, "poll_every": args.poll_every}
+
     def step(m, use_model):
         if use_model:
             plan(g.h, tr.h, d_roots, feats, ro, sp)
             tmotif.tm_count(g.h, tr.h, mode=m | tmotif.TM_SCHED_PLANNED, roots=ro, counts=counts, root_split=sp,
-                            stream=stream)
+                            stream=stream, tune=tune)
         else:
-            tmotif.tm_count(g.h, tr.h, mode=m, roots=d_roots, counts=counts, stream=stream)
+            tmotif.tm_count(g.h, tr.h, mode=m, roots=d_roots, counts=counts, stream=stream, tune=tune)
 
     def timed(m, use_model, n):
         ts = []
@@ -652,9 +660,9 @@ def main():
     # stats of one untimed launch of the same schedule: algorithmic bytes and work counters
     if use_model:
         _, st = tmotif.tm_count(g.h, tr.h, mode=mode | tmotif.TM_SCHED_PLANNED, roots=ro, root_split=sp,
-                                stats=True, stream=stream)
+                                stats=True, stream=stream, tune=tune)
     else:
-        _, st = tmotif.tm_count(g.h, tr.h, mode=mode, roots=roots, stats=True, stream=stream)
+        _, st = tmotif.tm_count(g.h, tr.h, mode=mode, roots=roots, stats=True, stream=stream, tune=tune)
 
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     if world > 1:
@@ -710,9 +718,10 @@ def main():
                 f2 = torch.empty((R, tmotif.TM_FEATURES), dtype=torch.float32, device="cuda")
                 ro2, sp2 = torch.empty_like(r2), torch.empty_like(r2)
                 plan(g2.h, tr2.h, r2, f2, ro2, sp2)
-                c2 = tmotif.tm_count(g2.h, tr2.h, mode=mode | tmotif.TM_SCHED_PLANNED, roots=ro2, root_split=sp2)
+                c2 = tmotif.tm_count(g2.h, tr2.h, mode=mode | tmotif.TM_SCHED_PLANNED, roots=ro2, root_split=sp2,
+                                     tune=tune)
             else:
-                c2 = tmotif.tm_count(g2.h, tr2.h, mode=mode, roots=h_roots)
+                c2 = tmotif.tm_count(g2.h, tr2.h, mode=mode, roots=h_roots, tune=tune)
             g2.close()
             tr2.close()
             times.append(time.perf_counter() - t0)
@@ -736,6 +745,8 @@ def main():
         "counts": ref_counts.cpu().tolist(),
         "schedule": ("learned plan (features, MLP, sorted slices) + reactive splitting" if use_model
                      else ("static, one warp per root" if args.static else "reactive splitting")),
+        "tunables": {"unit_work": args.unit_work, "max_split": args.max_split, "poll_every": args.poll_every,
+                     "donate_leaf": args.donate_leaf},
         "reactive_ms_per_step": reactive,
         "learned_speedup_vs_reactive": (reactive / ms_step) if reactive else None,
         "permotif_ms_per_step": perm,
