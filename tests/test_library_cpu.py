@@ -107,3 +107,26 @@ def test_header_cites_the_paper():
     txt = open(os.path.join(ROOT, "include", "tmotif.h")).read()
     for s in ("Section 2", "Algorithm 2", "Algorithm 3", "Algorithm 1", "Section 4.2"):
         assert s in txt
+
+
+def test_new_entry_points_check_arguments_on_the_host(lib):
+    """Argument checks that run before any device work: a NULL handle or output."""
+    import ctypes
+    tr = tmotif.Tree([((0, 1), (1, 2))], 10)
+    args = tmotif.tm_count_args()
+    n = ctypes.c_int64(0)
+    out = ctypes.c_int32(0)
+    assert lib.tm_enumerate(None, tr.h, ctypes.byref(args), None, 0, ctypes.byref(n), None, None) == tmotif.TM_EINVAL
+    assert lib.tm_enumerate(None, tr.h, None, None, 0, ctypes.byref(n), None, None) == tmotif.TM_EINVAL
+    assert lib.tm_graph_bipartite(None, ctypes.byref(out), None) == tmotif.TM_EINVAL
+    assert lib.tm_comine_advice(None, tr.h, ctypes.byref(out), None) == tmotif.TM_EINVAL
+    assert "NULL" in lib.tm_last_error().decode()
+    tr.close()
+
+
+def test_auto_mode_and_threshold_are_declared():
+    txt = open(os.path.join(ROOT, "include", "tmotif.h")).read()
+    assert "#define TM_AUTO 0x2u" in txt and tmotif.TM_AUTO == 0x2
+    assert "#define TM_COMINE_MIN_SM 0.44" in txt and tmotif.TM_COMINE_MIN_SM == 0.44
+    # one match record: motif, n_edges, TM_MAX_EDGES edge ids, all int32
+    assert tmotif.MATCH_FIELDS == 2 + tmotif.TM_MAX_EDGES
