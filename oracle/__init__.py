@@ -56,6 +56,8 @@ def _load():
         lib.oracle_count_motif_mt.argtypes = [P, P, P, i64, i32, P, P, ctypes.c_int, i64, P, i64,
                                               ctypes.c_int, ctypes.c_double, P, P]
         lib.oracle_count_motif_mt.restype = ctypes.c_int
+        lib.oracle_enumerate_motif.argtypes = [P, P, P, i64, i32, P, P, ctypes.c_int, i64, P, i64, P, i64, P]
+        lib.oracle_enumerate_motif.restype = ctypes.c_int
         _lib = lib
     return _lib
 
@@ -108,6 +110,28 @@ def count_motif(src, dst, t, motif: Sequence, delta: int, roots=None, n_nodes=No
             out.append(wk)
         return tuple(out)
     return total
+
+
+def enumerate_motif(src, dst, t, motif: Sequence, delta: int, roots=None, n_nodes=None, cap: int = 1 << 22):
+    """Algorithm 1, recording each match it completes.
+
+    Returns ``(matches, total)``: an int32 array of shape (min(total, cap), m)
+    with the edge ids of each match in motif edge order, and the number of
+    matches.
+    """
+    src, dst, t, V = _graph(src, dst, t, n_nodes)
+    m = mgtree.canonical(motif)
+    mu = np.array([e[0] for e in m], np.int8)
+    mv = np.array([e[1] for e in m], np.int8)
+    r = None if roots is None else np.ascontiguousarray(roots, np.int32)
+    nr = len(src) if r is None else len(r)
+    out = np.zeros((max(cap, 1), len(m)), np.int32)
+    n = ctypes.c_int64(0)
+    rc = _load().oracle_enumerate_motif(_p(src), _p(dst), _p(t), len(src), V, _p(mu), _p(mv), len(m),
+                                        int(delta), _p(r), nr, _p(out), int(cap), ctypes.byref(n))
+    if rc < 0:
+        raise ValueError("oracle rejected the motif or delta")
+    return out[:min(n.value, cap)], int(n.value)
 
 
 def count_motifs(src, dst, t, motifs, deltas, roots=None, n_nodes=None, per_root=False):

@@ -13,7 +13,8 @@
  *
  * Two procedures, each a plain recursion:
  *   - oracle_count_motif: Algorithm 1 (TemporalMining / MatchEdge /
- *     RollOnEdge / RollBackEdge), one motif at a time;
+ *     RollOnEdge / RollBackEdge), one motif at a time (oracle_enumerate_motif
+ *     runs the same recursion and also records each match it completes);
  *   - oracle_comine: Algorithm 3 (TemporalCoMining / CoMatchEdge) guided by
  *     a Motif-Group Tree given as a node table.
  *
@@ -72,6 +73,8 @@ typedef struct {
     int m;
     const int8_t *mu, *mv;
     int64_t count;
+    int32_t *rec;       /* enumeration: completed matches, m edge ids each (NULL: count only) */
+    int64_t rec_cap;    /* ... room for this many */
     /* tree (Algorithm 3) */
     int n_nodes;
     const int32_t *node_len;      /* |C_N| */
@@ -183,7 +186,12 @@ static void match_one_edge(og_ctx *c, int node, int em, int uM, int vM, descend_
 
 static void match_edge(og_ctx *c, int unused_node, int em) {
     (void)unused_node;
-    if (em == c->m) { c->count++; return; }   /* match found */
+    if (em == c->m) {                          /* match found: record it, count it */
+        if (c->rec && c->count < c->rec_cap)
+            memcpy(c->rec + c->count * c->m, c->e_stack, sizeof(int32_t) * (size_t)c->m);
+        c->count++;
+        return;
+    }
     match_one_edge(c, 0, em, c->mu[em], c->mv[em], match_edge);
 }
 
@@ -264,6 +272,38 @@ int oracle_count_motif(const int32_t *src, const int32_t *dst, const int64_t *t,
     free_ctx(c);
     free_adj(&g);
     return rc;
+}
+
+/*
+ * The matches themselves (Algorithm 1 records each match it completes):
+ * every tuple counted by oracle_count_motif over `roots` (NULL: all edges),
+ * written as m edge ids in motif edge order to out[0 .. min(total, cap) * m)
+ * in search order; *n_found gets the total.  Returns 0, or -1 for invalid
+ * input.
+ */
+int oracle_enumerate_motif(const int32_t *src, const int32_t *dst, const int64_t *t, int64_t E, int32_t V,
+                           const int8_t *mu, const int8_t *mv, int m, int64_t delta,
+                           const int32_t *roots, int64_t n_roots, int32_t *out, int64_t cap, int64_t *n_found) {
+    if (m < 1 || m > OR_MAXE || delta < 0 || cap < 0) return -1;
+    for (int i = 0; i < m; i++)
+        if (mu[i] < 0 || mv[i] < 0 || mu[i] >= OR_MAXV || mv[i] >= OR_MAXV || mu[i] == mv[i]) return -1;
+    og_graph g = {E, V, src, dst, t, 0, 0, 0, 0};
+    build_adj(&g);
+    og_ctx *c = new_ctx(&g);
+    c->m = m; c->mu = mu; c->mv = mv;
+    c->rec = out; c->rec_cap = out ? cap : 0;
+    int64_t nr = roots ? n_roots : E;
+    for (int64_t i = 0; i < nr; i++) {
+        int32_t r = roots ? roots[i] : (int32_t)i;
+        if (start_root(c, r, mu[0], mv[0], delta)) {
+            match_edge(c, 0, 1);
+            roll_back(c, src[r], dst[r]);
+        }
+    }
+    *n_found = c->count;
+    free_ctx(c);
+    free_adj(&g);
+    return 0;
 }
 
 /* ---------------------------------------------------------------- Algorithm 3 */

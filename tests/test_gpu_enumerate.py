@@ -1,5 +1,6 @@
 """Match enumeration (tm_enumerate) against brute force on tiny graphs, and
-against the definition, the oracle's counts and tm_count at larger sizes:
+against the oracle's recorded matches, the definition, the oracle's counts and
+tm_count at larger sizes:
 every written record must be a match, no two records equal, and as many
 records per motif as the count, which makes the set exact."""
 import numpy as np
@@ -96,6 +97,12 @@ def test_enumeration_tiny_workload_sample(tiny):
     ref = [oracle.count_motif(src, dst, t, m, synth.TINY_DELTA, roots=roots, n_nodes=2000) for m in motifs]
     assert counts.tolist() == ref
     _check_exact(src, dst, t, motifs, deltas, matches, counts)
+    # the oracle's own match lists (Algorithm 1 recording its matches)
+    recs = _records(matches, motifs)
+    for mi, motif in enumerate(motifs):
+        want, n = oracle.enumerate_motif(src, dst, t, motif, synth.TINY_DELTA, roots=roots, n_nodes=2000)
+        assert n == counts[mi]
+        assert sorted(e for m, e in recs if m == mi) == sorted(map(tuple, want.tolist()))
     tr.close()
 
 

@@ -293,3 +293,25 @@ def test_sparse_root_sample_is_distinct_sorted_and_seeded():
     assert np.array_equal(a, b) and len(set(a.tolist())) == 500
     assert np.all(np.diff(a) > 0) and a.min() >= 0 and a.max() < 10**9
     assert not np.array_equal(a, synth.root_sample_sparse(6, 10**9, 500))
+
+
+@pytest.mark.parametrize("seed", range(8))
+def test_oracle_enumeration_matches_brute_force(seed):
+    """The recorded matches of Algorithm 1 are exactly the brute-force match list,
+    on tie-heavy graphs with a self-loop, for every candidate-list case."""
+    rng = np.random.default_rng(900 + seed)
+    V, E = 6, 26
+    src = rng.integers(0, V, E).astype(np.int32)
+    dst = ((src + rng.integers(1, V, E)) % V).astype(np.int32)
+    src[5] = dst[5]
+    t = np.sort(rng.integers(0, 50, E)).astype(np.int64)
+    for motif in [((0, 1), (1, 2)), ((0, 1), (1, 0), (0, 1)), ((0, 1), (0, 2), (0, 3)),
+                  ((0, 1), (2, 1), (1, 3)), ((0, 1), (2, 3)), ((0, 1), (1, 2), (2, 0))]:
+        for delta in (0, 12, 50):
+            got, n = oracle.enumerate_motif(src, dst, t, motif, delta)
+            want = refimpl.brute_force_matches(src, dst, t, motif, delta)
+            assert n == len(want) == len(got)
+            assert sorted(map(tuple, got.tolist())) == sorted(want)
+    # a full buffer keeps the exact total
+    got, n = oracle.enumerate_motif(src, dst, t, ((0, 1), (1, 2)), 50, cap=3)
+    assert n == len(refimpl.brute_force_matches(src, dst, t, ((0, 1), (1, 2)), 50)) and len(got) == min(3, n)
