@@ -273,7 +273,6 @@ int enumerate(const tm_graph *g, const tm_tree *tr, const tm_count_args *args, t
     const int n_m = tr->h.n_motifs;
     int64_t n_roots = 0, root_lo = 0;
     const int32_t *roots = nullptr;
-    std::vector<int32_t> none;
     if (args->roots) {
         n_roots = args->n_roots;
         roots = args->roots;
