@@ -193,7 +193,13 @@ typedef struct {
  *           synchronises `stream`
  * Roots: every edge is a candidate for the first motif edge (Algorithm 1,
  * first call); counts are additive over roots, so a root list or range
- * yields the counts of matches whose first edge is in it.  Errors:
+ * yields the counts of matches whose first edge is in it.  A host root list
+ * is range-checked before launch; a device list (TM_ROOTS_DEVICE) is checked
+ * by the kernel, which skips a root outside [0, n_edges) and reports
+ * TM_EINVAL when the call synchronises (host counts, stats or a
+ * TM_SCHED_* mode); with device counts and static scheduling such a root
+ * only counts nothing.  per_root_counts, per_root_work and root_split must
+ * hold n_roots rows (the library cannot check their lengths).  Errors:
  * TM_EINVAL (NULL handle, root out of range, n_roots < 0); TM_ETIMEOUT if a
  * bounded device wait of TM_SCHED_DYNAMIC ran out (counts are then invalid);
  * TM_ECUDA; TM_ENOMEM.
@@ -361,11 +367,16 @@ int tm_autotune(const tm_graph *g, const tm_tree *tr, const tm_count_args *args,
  *           [root_lo, root_hi) (root_hi <= 0 means n_edges)
  *   counts: device array of n_motifs int64, overwritten; the call does not
  *           synchronise `stream`
- * Limits: at most 1024 motifs and a tree node table of at most 240 KiB
- * (about 3000 nodes); beyond them the call returns TM_EUNSUPPORTED.
+ *   Each device root must lie in [0, n_edges); the list is not read on the
+ *   host, and the kernel skips a root outside that range (it counts nothing
+ *   and no error is returned, as the call does not synchronise).
+ * Limits: at most 1024 motifs; any tree within TM_MAX_NODES nodes fits.
+ * Beyond 1024 motifs the call returns TM_EUNSUPPORTED.
  * Set-up: the first call on a device (made with that device current)
- * looks up the address of the static array there; make that first call
- * before any stream capture.  All calls share the one array, which keeps the
+ * looks up the address of the static array there and caches it for the
+ * life of the process, which assumes the device is not reset
+ * (cudaDeviceReset) in between; make that first call before any stream
+ * capture.  All calls share the one array, which keeps the
  * last call's contents; each call clears its counters itself, but calls
  * whose work overlaps on the GPU (several streams or threads at once) race
  * on the array and give wrong counts, so serialise them.

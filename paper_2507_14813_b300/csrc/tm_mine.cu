@@ -79,13 +79,16 @@ struct __align__(16) Task {
 };
 static_assert(sizeof(Task) == 64, "task layout");
 
+enum : int { kErrTimeout = 1,          // a bounded wait expired
+             kErrBadRoot = 2 };        // a root edge id outside [0, E) was skipped
+
 struct QueueHdr {
     unsigned long long root_cursor;
     unsigned int head;        // next task to claim
     unsigned int tail;        // tasks reserved by donors
     int idle;                 // warps waiting for work
     int busy;                 // warps holding work
-    int error;                // bit 0: a bounded wait expired
+    int error;                // kErr* bits
     int pad;
 };
 
@@ -775,7 +778,7 @@ struct Miner {
             if (slot >= 0) {
                 long long spins = 0;
                 while (vload(p.ready + slot) == 0) {
-                    if (++spins > kReadySpins) { atomicOr(&p.q->error, 1); slot = -2; break; }
+                    if (++spins > kReadySpins) { atomicOr(&p.q->error, kErrTimeout); slot = -2; break; }
                     __nanosleep(64);
                 }
                 __threadfence();
@@ -1147,6 +1150,10 @@ __global__ void __launch_bounds__(kThreads, TM_MIN_BLOCKS) k_mine(Params p) {
                 M.split_h = p.split ? __ldg(p.split + ri) : 0;
                 M.rmask = p.root_qmask ? __ldg(p.root_qmask + ri) : ~0ull;
                 const int32_t r = p.roots ? __ldg(p.roots + ri) : (int32_t)(p.root_lo + ri);
+                if (r < 0 || r >= p.g.E) {                  // a device root list is not checked on the host
+                    if (lane == 0) atomicOr(&p.q->error, kErrBadRoot);
+                    continue;
+                }
                 Work before = M.w;
                 M.root(r);
                 if (kStats && lane == 0) M.w.v[kStRoots]++;
@@ -1425,8 +1432,10 @@ int mine(const tm_graph *g, const tm_tree *tr, const tm_count_args *args, int64_
     if (rc != TM_OK) return finish(rc);
     if (stats) cudaEventRecord(e1, s);
 
-    // the dynamic mode reports expired waits; that needs the queue headers back
-    if (P.dynamic) {
+    // error bits (expired waits, skipped device roots) come back with the
+    // queue headers whenever the call synchronises anyway; the dynamic mode
+    // always synchronises for them
+    if (P.dynamic || !dev_counts || stats) {
         std::vector<QueueHdr> hq(P.n_launch);
         cudaMemcpyAsync(hq.data(), scratch + P.o_q, sizeof(QueueHdr) * P.n_launch, cudaMemcpyDeviceToHost, s);
         cudaError_t e = cudaStreamSynchronize(s);
@@ -1434,11 +1443,16 @@ int mine(const tm_graph *g, const tm_tree *tr, const tm_count_args *args, int64_
             set_error(std::string("tm_count: ") + cudaGetErrorString(e));
             return finish(TM_ECUDA);
         }
-        for (auto &q : hq)
-            if (q.error) {
+        for (auto &q : hq) {
+            if (q.error & kErrTimeout) {
                 set_error("tm_count: a bounded device wait expired; counts are incomplete");
                 return finish(TM_ETIMEOUT);
             }
+            if (q.error & kErrBadRoot) {
+                set_error("tm_count: a device root edge id is outside [0, n_edges)");
+                return finish(TM_EINVAL);
+            }
+        }
     }
     const unsigned long long *d_cnt = (const unsigned long long *)scratch;
     if (dev_counts) {
@@ -1561,9 +1575,13 @@ extern "C" int tm_exec_status(tm_exec *x, void *stream) {
     int32_t st = 0;
     TM_CUDA_TRY(cudaMemcpyAsync(&st, x->status, 4, cudaMemcpyDeviceToHost, (cudaStream_t)stream));
     TM_CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
-    if (st) {
+    if (st & kErrTimeout) {
         set_error("tm_exec: a bounded device wait expired in the last replay; its counts are incomplete");
         return TM_ETIMEOUT;
+    }
+    if (st & kErrBadRoot) {
+        set_error("tm_exec: a device root edge id is outside [0, n_edges)");
+        return TM_EINVAL;
     }
     return TM_OK;
 }
@@ -1658,12 +1676,20 @@ constexpr size_t kNoAllocTree = 16u << 10;            // tree image from 16 KiB 
 constexpr size_t kNoAllocMaxTree = kNoAllocBytes - kNoAllocTree;
 constexpr int kNoAllocMaxDevices = 64;
 
+// the largest tree image: TM_MAX_NODES nodes, one ref per motif, the window
+// and query tables, each section 256-byte aligned
+static_assert(sizeof(DevNode) * TM_MAX_NODES + 256 + sizeof(DevRef) * kNoAllocMaxMotifs + 256 +
+                      sizeof(int64_t) * TM_MAX_DELTAS + 256 + 64 + 256 <= kNoAllocMaxTree,
+              "every tree within the limits fits the static scratch");
+
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 
 std::mutex g_noalloc_mu;
 void *g_noalloc_ptr[kNoAllocMaxDevices];
 
-// Device address of the static array on the current device (looked up once per device).
+// Device address of the static array on the current device, looked up once
+// per device and cached: the cache assumes the device's primary context is
+// not reset (cudaDeviceReset) while the library is loaded.
 int noalloc_scratch(int dev, void **out) {
     std::lock_guard<std::mutex> lk(g_noalloc_mu);
     if (!g_noalloc_ptr[dev]) {
@@ -1692,8 +1718,8 @@ extern "C" int tm_count_noalloc(const tm_graph *g, const tm_tree *tr, const int3
         return TM_EUNSUPPORTED;
     }
     const TreeImage &img = tr->image;
-    if (img.bytes.size() > kNoAllocMaxTree) {
-        set_error("tm_count_noalloc: tree node table larger than 240 KiB does not fit its static scratch");
+    if (img.bytes.size() > kNoAllocMaxTree) {   // cannot happen within the limits (static_assert above)
+        set_error("tm_count_noalloc: tree node table larger than its static scratch");
         return TM_EUNSUPPORTED;
     }
     if (roots) {

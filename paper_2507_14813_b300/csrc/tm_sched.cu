@@ -75,6 +75,11 @@ __global__ void k_features(DevGraph g, const int32_t *roots, int64_t n, int64_t 
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const int32_t r = roots[i];
+    float *x = X + i * kIn;
+    if (r < 0 || r >= g.E) {                 // a root outside the graph has no features
+        for (int f = 0; f < kIn; f++) x[f] = 0.f;
+        return;
+    }
     const int32_t a = __ldg(g.src + r), b = __ldg(g.dst + r);
     const int64_t t0 = __ldg(g.t + r);
     const int64_t lim = (delta > 0 && t0 > INT64_MAX - delta) ? INT64_MAX : t0 + delta;
@@ -85,7 +90,6 @@ __global__ void k_features(DevGraph g, const int32_t *roots, int64_t n, int64_t 
     const float wob = (float)(ub(g.out_adj, ob0, ob1, hi) - ub(g.out_adj, ob0, ob1, r));
     const float wib = (float)(ub(g.in_adj, ib0, ib1, hi) - ub(g.in_adj, ib0, ib1, r));
     const float woa = (float)(ub(g.out_adj, oa0, oa1, hi) - ub(g.out_adj, oa0, oa1, r));
-    float *x = X + i * kIn;
     x[0] = log1pf((float)(ob1 - ob0));
     x[1] = log1pf((float)(ib1 - ib0));
     x[2] = log1pf((float)(oa1 - oa0));

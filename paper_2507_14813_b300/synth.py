@@ -378,3 +378,26 @@ def tiny_graph(seed: int, n_nodes: int, n_edges: int, t_max: int, zipf_s: float 
         dst[bad] = (src[bad] + 1) % n_nodes
     t = (rand_uniform(seed, 13, 0, n_edges) * t_max).astype(np.int64)
     return sort_edges(src, dst, t)
+
+
+def hub_graph(seed: int, n_nodes: int, n_edges: int, t_max: int, hub_out: float = 0.5, hub_in: float = 0.25,
+              zipf_s: float = 0.8):
+    """A graph with one hub (vertex 0): a fraction hub_out of the edges leave
+    it and hub_in enter it; the other endpoints are Zipf(zipf_s) over
+    vertices 1..n_nodes-1, so a hub window holds many distinct far ends with
+    a few frequent ones; the remaining edges join two such vertices.
+    Integer times uniform in [0, t_max) (tie-heavy when n_edges > t_max)."""
+    u = rand_uniform(seed, 16, 0, n_edges)
+    cdf = zipf_cdf(n_nodes - 1, zipf_s)
+    a = (1 + zipf_draw(cdf, rand_uniform(seed, 17, 0, n_edges))).astype(np.int32)
+    b = (1 + zipf_draw(cdf, rand_uniform(seed, 18, 0, n_edges))).astype(np.int32)
+    src = a.copy()
+    dst = b.copy()
+    out_hub = u < hub_out
+    in_hub = (u >= hub_out) & (u < hub_out + hub_in)
+    src[out_hub] = 0
+    dst[in_hub] = 0
+    same = src == dst
+    dst[same] = 1 + (dst[same] % (n_nodes - 1))
+    t = (rand_uniform(seed, 19, 0, n_edges) * t_max).astype(np.int64)
+    return sort_edges(src.astype(np.int32), dst.astype(np.int32), t)

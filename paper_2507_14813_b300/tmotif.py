@@ -42,6 +42,10 @@ TM_MODEL_PARAMS = 4801
 TM_ROOTS_DEVICE = 0x1
 TM_COUNTS_DEVICE = 0x2
 
+TM_WORK_CANDIDATES = 0
+TM_WORK_EXPANSIONS = 1
+TM_WORK_PROBES = 2
+TM_WORK_LEAF_EVALS = 3
 TM_WORK_FIELDS = 4
 WORK_NAMES = ("candidates", "expansions", "probes", "leaf_evals")
 
@@ -350,8 +354,18 @@ def tm_count(g, tr, mode: int = TM_COMINE, roots=None, root_lo: int = 0, root_hi
         pc = out.ctypes.data_as(ctypes.c_void_p)
     else:
         pc, on_dev, out = _ptr(counts, np.int64)
+        if len(out.reshape(-1)) < n_motifs:
+            raise ValueError("counts holds %d values; the tree has %d motifs" % (len(out.reshape(-1)), n_motifs))
         if on_dev:
             a.flags |= TM_COUNTS_DEVICE
+    n_roots = a.n_roots if roots is not None else (
+        (root_hi if root_hi > 0 else tm_graph_get_info(g)["n_edges"]) - root_lo)
+    # the library writes [n_roots][fields] per-root outputs and reads n_roots
+    # slices; it cannot see the tensors' lengths
+    for name, arr, per in (("per_root_counts", per_root_counts, n_motifs),
+                           ("per_root_work", per_root_work, TM_WORK_FIELDS), ("root_split", root_split, 1)):
+        if arr is not None and arr.numel() < max(n_roots, 0) * per:
+            raise ValueError("%s holds %d values; %d roots need %d" % (name, arr.numel(), n_roots, n_roots * per))
     st = tm_run_stats()
     _check(lib().tm_count(g, tr, ctypes.byref(a), pc, ctypes.byref(st) if stats else None, _stream(stream)))
     return (out, st.as_dict()) if stats else out
@@ -393,6 +407,10 @@ def tm_count_noalloc(g, tr, counts, roots=None, root_lo: int = 0, root_hi: int =
     pc, on_dev, keep_c = _ptr(counts, np.int64)
     if not on_dev:
         raise TypeError("counts must be a CUDA tensor")
+    n_motifs = tm_tree_get_info(tr)["n_motifs"]
+    if counts.numel() < n_motifs:
+        # the library writes n_motifs values and cannot see the tensor's length
+        raise ValueError("counts holds %d values; the tree has %d motifs" % (counts.numel(), n_motifs))
     pr, n = None, 0
     if roots is not None:
         pr, r_dev, keep_r = _ptr(roots, np.int32)

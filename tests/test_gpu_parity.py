@@ -14,6 +14,7 @@ from tests.test_oracle_pins import PIN_MOTIFS
 pytestmark = pytest.mark.gpu
 
 D = tmotif.TM_SCHED_DYNAMIC
+P = tmotif.TM_SCHED_PLANNED
 MODES = [
     ("comine", tmotif.TM_COMINE),
     ("comine-scan", tmotif.TM_COMINE | tmotif.TM_LEAF_SCAN),
@@ -22,7 +23,19 @@ MODES = [
     ("comine-dyn", tmotif.TM_COMINE | D),
     ("comine-scan-dyn", tmotif.TM_COMINE | tmotif.TM_LEAF_SCAN | D),
     ("permotif-dyn", tmotif.TM_PERMOTIF | D),
+    ("comine-planned", tmotif.TM_COMINE | P),
+    ("comine-planned-dyn", tmotif.TM_COMINE | P | D),
+    ("permotif-scan-planned", tmotif.TM_PERMOTIF | tmotif.TM_LEAF_SCAN | P),
 ]
+
+
+def count_mode(g, tr, mode, n_edges, **kw):
+    """tm_count over every root edge; a planned mode cuts each root's
+    first-level lists into 4 slices."""
+    if mode & P:
+        import torch
+        kw["root_split"] = torch.full((n_edges,), 4, dtype=torch.int32, device="cuda")
+    return tmotif.count(g, tr, mode=mode, **kw)
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -43,7 +56,7 @@ def tiny():
 def test_tiny_config_full(tiny, name, mode):
     src, dst, t, g, want = tiny
     tr = tmotif.Tree(synth.CONFIG1_MOTIFS, synth.TINY_DELTA)
-    got = tmotif.count(g, tr, mode=mode)
+    got = count_mode(g, tr, mode, len(src))
     assert got.tolist() == want.tolist(), name
 
 
@@ -80,7 +93,7 @@ def test_pin_motifs_small_graphs(seed, name, mode):
     g = tmotif.Graph(src, dst, t, 9 + seed, presorted=True)
     tr = tmotif.Tree(PIN_MOTIFS, deltas)
     want = [oracle.count_motif(src, dst, t, m, d, n_nodes=9 + seed) for m, d in zip(PIN_MOTIFS, deltas)]
-    got = tmotif.count(g, tr, mode=mode)
+    got = count_mode(g, tr, mode, len(src))
     assert got.tolist() == want
 
 
@@ -93,7 +106,7 @@ def test_random_trees_multi_delta(seed):
     tr = tmotif.Tree(motifs, deltas)
     want = [oracle.count_motif(src, dst, t, m, d, n_nodes=40) for m, d in zip(motifs, deltas)]
     for _, mode in MODES:
-        assert tmotif.count(g, tr, mode=mode).tolist() == want
+        assert count_mode(g, tr, mode, len(src)).tolist() == want
 
 
 def test_max_size_motifs():
@@ -107,7 +120,7 @@ def test_max_size_motifs():
     tr = tmotif.Tree(motifs, 150)
     want = [oracle.count_motif(src, dst, t, m, 150, n_nodes=8) for m in motifs]
     for _, mode in MODES:
-        assert tmotif.count(g, tr, mode=mode).tolist() == want
+        assert count_mode(g, tr, mode, len(src)).tolist() == want
 
 
 def test_unsorted_and_device_input():
@@ -176,6 +189,27 @@ def test_errors():
     assert e.value.code == tmotif.TM_EINVAL
 
 
+def test_device_roots_out_of_range(tiny):
+    """A device root list is range-checked by the kernel: the call reports
+    TM_EINVAL when it synchronises, and the binding rejects per-root outputs
+    shorter than the root list."""
+    import torch
+    src, dst, t, g, _ = tiny
+    tr = tmotif.Tree(synth.CONFIG1_MOTIFS, synth.TINY_DELTA)
+    for bad in (len(src), -1):
+        roots = torch.tensor([5, bad, 7], dtype=torch.int32, device="cuda")
+        for mode in (0, D):
+            with pytest.raises(tmotif.TMError) as e:
+                tmotif.count(g, tr, roots=roots, mode=mode)
+            assert e.value.code == tmotif.TM_EINVAL
+    roots = torch.tensor([5, 6, 7], dtype=torch.int32, device="cuda")
+    short = torch.zeros((2, 4), dtype=torch.int64, device="cuda")
+    with pytest.raises(ValueError):
+        tmotif.count(g, tr, roots=roots, per_root_counts=short)
+    assert tmotif.count(g, tr, roots=roots).tolist() == oracle.count_motifs(
+        src, dst, t, synth.CONFIG1_MOTIFS, synth.TINY_DELTA, roots=[5, 6, 7]).tolist()
+
+
 def test_stats_and_work_counters(tiny):
     import torch
     src, dst, t, g, want = tiny
@@ -191,7 +225,32 @@ def test_stats_and_work_counters(tiny):
     assert st["kernel_ms"] > 0
     # scan mode visits every leaf candidate: its candidate count bounds the leaf totals
     _, st2 = tmotif.count(g, tr, roots=roots, mode=tmotif.TM_LEAF_SCAN, stats=True)
-    assert st2["leaf_evals"] == 0 and st2["candidates"] >= got.sum() - st["leaf_evals"] * 0
+    assert st2["leaf_evals"] == 0 and st2["candidates"] >= got.sum()
+
+
+# motifs whose every level has exactly one mapped endpoint, so the kernel and
+# Algorithm 1 scan the same list at every level
+ONE_LIST = [((0, 1), (1, 2), (2, 3)), ((0, 1), (0, 2), (0, 3)), ((0, 1), (2, 1), (3, 1)), ((0, 1), (2, 1), (1, 3)),
+            ((0, 1), (1, 2), (1, 3), (3, 4))]
+
+
+@pytest.mark.parametrize("motif", ONE_LIST)
+def test_work_counters_equal_oracle_work(tiny, motif):
+    """Per-root work (a10) against an independent count: scanning each level
+    (TM_LEAF_SCAN, one warp per root) examines exactly the adjacency entries
+    inside the window after the previous match, which is the number of
+    candidates Algorithm 1 examines."""
+    import torch
+    src, dst, t, g, _ = tiny
+    roots = synth.root_sample(13, len(src), 3000)
+    tr = tmotif.Tree([motif], synth.TINY_DELTA)
+    work = torch.zeros((len(roots), tmotif.TM_WORK_FIELDS), dtype=torch.int64, device="cuda")
+    pr = torch.zeros((len(roots), 1), dtype=torch.int64, device="cuda")
+    tmotif.count(g, tr, roots=roots, per_root_work=work, per_root_counts=pr, mode=tmotif.TM_LEAF_SCAN, stats=True)
+    _, want_pr, want_work = oracle.count_motif(src, dst, t, motif, synth.TINY_DELTA, roots=roots, per_root=True,
+                                               work=True)
+    assert np.array_equal(pr.cpu().numpy()[:, 0], want_pr)
+    assert np.array_equal(work.cpu().numpy()[:, tmotif.TM_WORK_CANDIDATES], want_work)
 
 
 @pytest.fixture(scope="module")

@@ -7,6 +7,7 @@ import time
 import numpy as np
 import pytest
 
+import oracle
 from paper_2507_14813_b300 import build, synth, tmotif
 
 pytestmark = pytest.mark.gpu
@@ -52,6 +53,23 @@ def test_each_result_equals_alone(tiny, mode):
         alone = tmotif.count(g, tmotif.Tree(ms, d), roots=r)
         assert counts.tolist() == alone.tolist()
         assert st["latency_ms"] >= st["queue_ms"] >= 0
+
+
+@pytest.mark.parametrize("mode", [tmotif.TM_SCHED_DYNAMIC, tmotif.TM_LEAF_SCAN])
+def test_served_counts_equal_oracle(tiny, mode):
+    """Each served request's counts against the oracle (Algorithm 1 per motif
+    with the request's own window and roots, Section 2), while the requests
+    share merged trees and launches."""
+    src, dst, t, g = tiny
+    qs = _queries(24, len(src), seed0=1500)
+    srv = tmotif.Server(g, streams=3, max_batch=8, mode=mode)
+    tickets = [srv.submit(ms, d, r) for ms, d, r in qs]
+    results = [srv.poll(tk, wait=True) for tk in tickets]
+    srv.close()
+    assert max(st["batch_size"] for _, st in results) > 1
+    for (ms, d, r), (counts, _) in zip(qs, results):
+        want = [oracle.count_motif(src, dst, t, m, dm, roots=r, n_nodes=synth.TINY.n_nodes) for m, dm in zip(ms, d)]
+        assert counts.tolist() == want
 
 
 def test_arrivals_overlap_running_batches(tiny):

@@ -315,3 +315,22 @@ def test_oracle_enumeration_matches_brute_force(seed):
     # a full buffer keeps the exact total
     got, n = oracle.enumerate_motif(src, dst, t, ((0, 1), (1, 2)), 50, cap=3)
     assert n == len(refimpl.brute_force_matches(src, dst, t, ((0, 1), (1, 2)), 50)) and len(got) == min(3, n)
+
+
+@pytest.mark.parametrize("threads", [1, 3])
+def test_multithreaded_oracle_per_root_equals_single(threads):
+    """The timed CPU baseline's Algorithm 1 over roots (dynamic loop over
+    threads, time limit) gives the per-root counts of the plain recursion
+    when it finishes, and marks unreached roots -1 when it runs out of time."""
+    src, dst, t = synth.make_graph(synth.TINY)
+    roots = synth.root_sample(41, len(src), 2000)
+    for m in synth.CONFIG1_MOTIFS + [((0, 1), (0, 2), (0, 3))]:
+        _, want = oracle.count_motif(src, dst, t, m, synth.TINY_DELTA, roots=roots, per_root=True)
+        got, done = oracle.count_motif_timed(src, dst, t, m, synth.TINY_DELTA, roots, threads=threads,
+                                             time_limit=600.0)
+        assert done == len(roots)
+        assert np.array_equal(got, want), m
+    # a limit that has passed before the first root: nothing is reached
+    got, done = oracle.count_motif_timed(src, dst, t, synth.CONFIG1_MOTIFS[2], synth.TINY_DELTA, roots,
+                                         threads=threads, time_limit=1e-9)
+    assert done == int((got >= 0).sum()) and done < len(roots)
