@@ -11,7 +11,9 @@ roots x motifs / step time.  Under torchrun every rank mines its own root
 sample (weak scaling, no collective on the data path).
 
 ``--impl reference`` times the CPU oracle (the plain recursion of
-Algorithm 1 per motif, all host cores) on a bounded part of the same sample.
+Algorithm 1 per motif, all host cores) on the same roots and motifs at a
+window it finishes (CPU_SAMPLE_DELTA); the CPU-baseline leg of the default
+run times the same sample on one core and on all cores, and the GPU on it.
 """
 from __future__ import annotations
 
@@ -152,20 +154,35 @@ def cpu_model():
     return None
 
 
-def cpu_baseline(src, dst, t, motifs, delta, roots, seconds=20.0, threads=1):
-    """Oracle (Algorithm 1 per motif) on a bounded part of the root sample."""
+# The CPU oracle does not finish the mid workload's hub roots at delta = 3600 s
+# (a 4-edge star on one hub root has ~10^14 matches), so the CPU baseline and
+# the reference arm run the same 64 roots and 12 motifs at this window, which
+# the oracle finishes for every root in ~10 s on one core; the GPU step is
+# timed on the same sample beside it.
+CPU_SAMPLE_DELTA = 15
+
+
+def cpu_sample(src, dst, t, motifs, roots, threads=1):
+    """Oracle (Algorithm 1 per motif) over every root of the sample at
+    CPU_SAMPLE_DELTA: (counts per motif, roots finished, wall seconds)."""
     import oracle
-    per_motif = seconds / len(motifs)
-    t_root = 0.0
-    done_min = len(roots)
+    t0 = time.perf_counter()
+    counts, done = [], len(roots)
     for m in motifs:
-        t0 = time.perf_counter()
-        _, done = oracle.count_motif_timed(src, dst, t, m, delta, roots, threads=threads, time_limit=per_motif)
-        el = time.perf_counter() - t0
-        done_min = min(done_min, done)
-        t_root += el / max(done, 1)            # seconds per root for this motif
-    value = len(motifs) / t_root               # query root-edges per second
-    return value, done_min
+        if threads == 1:
+            _, pr = oracle.count_motif(src, dst, t, m, CPU_SAMPLE_DELTA, roots=roots, per_root=True)
+        else:
+            pr, _ = oracle.count_motif_timed(src, dst, t, m, CPU_SAMPLE_DELTA, roots, threads=threads,
+                                             time_limit=0)
+        done = min(done, int((pr >= 0).sum()))
+        counts.append(int(pr[pr >= 0].sum()))
+    return counts, done, time.perf_counter() - t0
+
+
+def cpu_sample_text(n_roots, n_motifs, done, workload_delta):
+    return ("the %d roots of the benchmark sample x %d motifs at delta = %d s instead of %d s (the oracle does not "
+            "finish hub roots at the full window); %d of %d roots finished" %
+            (n_roots, n_motifs, CPU_SAMPLE_DELTA, workload_delta, done, n_roots))
 
 
 def plan_launches(n_roots):
@@ -511,27 +528,36 @@ def run_enumerate(args):
 
 
 def run_reference(args):
+    """The oracle on the host cores, each step the CPU sample (the benchmark's
+    roots and motifs at CPU_SAMPLE_DELTA), timed by the wall clock."""
     rank, local_rank, world = env_rank()
     if rank != 0:
         return 0
     spec, src, dst, t, motifs, delta, roots = load_workload(args.workload, args.roots, 0)
     threads = os.cpu_count() or 1
-    steps = []
+    secs, done, counts = [], len(roots), None
     for i in range(args.warmup + args.steps):
-        v, done = cpu_baseline(src, dst, t, motifs, delta, roots, seconds=args.ref_seconds, threads=threads)
+        c, d, el = cpu_sample(src, dst, t, motifs, roots, threads=threads)
+        if counts is not None and c != counts:
+            raise SystemExit("oracle counts changed between steps")
+        counts, done = c, min(done, d)
         if i >= args.warmup:
-            steps.append(v)
-    value = statistics.median(steps)
-    sample = ("first roots of the %d-root sample reached within %.0f s per step (%d of %d for the slowest motif)"
-              % (len(roots), args.ref_seconds, done, len(roots)))
+            secs.append(el)
+    step_s = statistics.median(secs)
+    units = len(roots) * len(motifs)
+    value = units / step_s
+    cfg = config_of(args, spec, motifs, delta, roots)
+    cfg["sample_delta"] = CPU_SAMPLE_DELTA
     line = {
         "impl": "reference", "metric": "query root-edges/sec (roots x motifs / s), exact co-mining",
         "value": value, "unit": "root-edges/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": 1000.0 * len(roots) * len(motifs) / value, "higher_is_better": True,
+        "ms_per_step": 1000.0 * step_s, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
-        "config": config_of(args, spec, motifs, delta, roots),
+        "config": cfg,
         "cpu_baseline": {"value": value, "unit": "root-edges/s", "cores": threads, "kind": "oracle",
-                         "sample": sample},
+                         "cpu": cpu_model(), "sample": cpu_sample_text(len(roots), len(motifs), done, delta),
+                         "seconds_per_step": step_s},
+        "counts": counts,
         "e2e": {"value": value, "unit": "root-edges/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
@@ -555,8 +581,6 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="mid", choices=sorted(WORKLOADS))
     ap.add_argument("--roots", type=int, default=0)
-    ap.add_argument("--ref-seconds", type=float, default=20.0)
-    ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-cpu-all-cores", action="store_true", help="skip the all-core oracle context figure")
     ap.add_argument("--no-e2e", action="store_true")
@@ -767,19 +791,39 @@ def main():
     if e2e:
         line["e2e"] = e2e
     if rank == 0 and not args.no_cpu_baseline:
-        v, done = cpu_baseline(src, dst, t, motifs, delta, roots, seconds=args.cpu_seconds, threads=1)
-        line["cpu_baseline"] = {"value": v, "unit": "root-edges/s", "cores": 1, "kind": "oracle",
-                                "cpu": cpu_model(),
-                                "sample": "first roots of the same sample reached in %.0f s (%d of %d for the "
-                                          "slowest motif), Algorithm 1 per motif" % (args.cpu_seconds, done, len(roots))}
+        units = len(roots) * n_m
+        c1, done, el = cpu_sample(src, dst, t, motifs, roots, threads=1)
+        # the GPU on the same sample: same roots and motifs, same window
+        tr_s = tmotif.Tree(motifs, CPU_SAMPLE_DELTA)
+        gs = tmotif.count(g, tr_s, roots=d_roots, mode=mode)
+        if gs.tolist() != c1:
+            raise SystemExit("GPU counts differ from the oracle's on the CPU sample")
+        ts = []
+        for i in range(max(args.steps, 3)):
+            flush.fill_(i & 0xFF)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            tmotif.tm_count(g.h, tr_s.h, mode=mode, roots=d_roots, counts=counts, stream=stream, tune=tune)
+            b.record(stream)
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b))
+        gms = statistics.median(ts)
+        sample = cpu_sample_text(len(roots), n_m, done, delta)
+        line["cpu_baseline"] = {"value": units / el, "unit": "root-edges/s", "cores": 1, "kind": "oracle",
+                                "cpu": cpu_model(), "sample": sample, "seconds": el,
+                                "counts_equal_gpu": True}
+        line["gpu_on_cpu_sample"] = {"value": units / (gms / 1000.0), "unit": "root-edges/s", "ms_per_step": gms,
+                                     "delta": CPU_SAMPLE_DELTA, "schedule": "reactive splitting",
+                                     "speedup_vs_cpu_one_core": el / (gms / 1000.0)}
         if not args.no_cpu_all_cores:
             n = os.cpu_count() or 1
-            v, done = cpu_baseline(src, dst, t, motifs, delta, roots, seconds=args.cpu_seconds, threads=n)
+            cn, done_n, el_n = cpu_sample(src, dst, t, motifs, roots, threads=n)
+            if cn != c1:
+                raise SystemExit("multithreaded oracle counts differ")
             line["cpu_baseline_all_cores"] = {
-                "value": v, "unit": "root-edges/s", "cores": n, "kind": "oracle", "cpu": cpu_model(),
+                "value": units / el_n, "unit": "root-edges/s", "cores": n, "kind": "oracle", "cpu": cpu_model(),
                 "context": "the same oracle with a dynamic OpenMP loop over roots on every host core",
-                "sample": "roots of the same sample finished within %.0f s (%d of %d for the slowest motif)"
-                          % (args.cpu_seconds, done, len(roots))}
+                "sample": cpu_sample_text(len(roots), n_m, done_n, delta), "seconds": el_n}
     if rank == 0:
         print(json.dumps(line))
     if world > 1:

@@ -933,9 +933,135 @@ struct Miner {
         step(k, base, end, fetch(ws.ltype[k], base, end));
     }
 
+    // The hot case of drain: a counting-only star frame whose work per
+    // survivor is one star leaf with one ref and, on the node's last level,
+    // the node's own refs, all counted in the frame's own window (the last
+    // two edges of an out- or in-star; the 3-star that is the 4-star's
+    // prefix).  Every survivor matches such a node ref, so those refs get the
+    // frame's survivor total at the end.  The frame's cursor, end and
+    // survivor suffix stay in registers and the mapped labels are read once;
+    // the shared-memory frame is brought up to date around a donation and at
+    // the end.  Counts, work counters and donations are those of the general
+    // loop.  Returns false (nothing done) when the level is not of that form.
+    __device__ bool drain_star(int k, int kbase) {
+        if (!ws.star[k]) return false;
+        const DevNode &N = p.tr.nodes[ws.node[k]];
+        const int32_t fhi = frame_hi(N);
+        const bool complete = (k == N.k_end - 1);
+        const DevNode *L = nullptr;
+        if (!complete) {
+            if ((N.flags & kNodeParLeaf) && k == N.k_end - 2) L = &N;
+        } else if (N.n_par == 1) {
+            L = &p.tr.nodes[N.child_begin + N.n_seq];
+            for (int i = 0; i < N.n_ref; i++) {
+                const DevRef r = p.tr.refs[N.ref_begin + i];
+                if (((rmask >> r.query) & 1ull) && ws.ehi[r.delta] != fhi) return false;
+            }
+        }
+        if (!L || !(L->flags & kNodeStarLeaf) || L->n_ref != 1) return false;
+        const DevRef ref = p.tr.refs[L->ref_begin];
+        if (!((rmask >> ref.query) & 1ull) || ws.ehi[ref.delta] != fhi) return false;
+
+        const int2 *adj = ws.ltype[k] == kListOut ? p.g.out_adj : p.g.in_adj;
+        const int nv = N.nvb[k];
+        int32_t lab[kMaxV];
+#pragma unroll
+        for (int l = 0; l < kMaxV; l++) lab[l] = l < nv ? ws.m2g[l] : -1;   // -1 is no vertex
+        const int8_t sm = ws.same_mode[k];
+        const bool own = ws.cache_owner == k;
+        const uint32_t above = (lane == 31) ? 0u : ~((2u << lane) - 1u);
+        int64_t pos = ws.pos[k], end = ws.end[k], suf = ws.suf[k];
+        const int64_t suf0 = suf;
+        unsigned long long acc_l = 0;
+        int64_t cb = max(pos, end - 32), ce = end;       // the chunk [cb, ce), scanned from the top
+        int2 c = (cb + lane < ce) ? __ldg(adj + cb + lane) : make_int2(0, 0);
+        while (true) {
+            end = cb;                                    // claimed: a donation cannot hand it out
+            if (p.react && ++polls >= p.poll_every) {
+                polls = 0;
+                __syncwarp();
+                if (lane == 0) {
+                    ws.end[k] = end;
+                    ws.pos[k] = pos;
+                }
+                __syncwarp();
+                maybe_donate(kbase, k);
+                pos = ws.pos[k];                         // a donation hands over the bottom part
+            }
+            const bool more = pos < end;
+            int64_t nb = 0;
+            int2 nc = make_int2(0, 0);
+            if (more) {
+                nb = max(pos, end - 32);
+                if (nb + lane < end) nc = __ldg(adj + nb + lane);
+            }
+            const bool valid = cb + lane < ce;
+            bool bad = false;
+#pragma unroll
+            for (int l = 0; l < kMaxV; l++) bad |= (c.x == lab[l]);
+            const bool ok = valid && !bad;
+            const uint32_t S = __ballot_sync(0xffffffffu, ok);
+            const uint32_t peers = (sm != kSameGallop) ? __match_any_sync(0xffffffffu, ok ? c.x : -1) : 0u;
+            int32_t known = -1;
+            if (ok) {
+                const int64_t later = suf + __popc(S & above);
+                int64_t same;
+                if (sm == kSameChunk) {
+                    same = __popc(peers & above);
+                } else {
+                    const uint32_t slot = ((uint32_t)c.x * 2654435761u) >> kSlotShift;
+                    const unsigned long long ent = sm == kSameTable ? ws.cslot[slot] : 0ull;
+                    const uint32_t key = (uint32_t)(ent >> 32);
+                    if (sm == kSameTable && key == (uint32_t)c.x) {
+                        same = (int64_t)(uint32_t)ent + __popc(peers & above);
+                    } else if (sm == kSameTable && key == kCacheEmpty) {
+                        same = __popc(peers & above);    // a value seen above would have claimed the slot
+                    } else {
+                        unsigned long long pr = 0;
+                        same = run_tail(p.g.pair_eid, __ldg(p.g.pr_pos + c.y), __ldg(p.g.pr_end + c.y), fhi, pr);
+                        if (kStats) w.v[kStPairProbe] += pr + 2;
+                    }
+                }
+                acc_l += (unsigned long long)(later - same);
+                known = (int32_t)same;
+                if (kStats) w.v[kStLeaf] += 1;
+            }
+            if (kStats) {
+                const uint32_t VB = __ballot_sync(0xffffffffu, valid);     // every lane votes
+                if (lane == 0) w.v[kStCand] += (unsigned long long)__popc(VB);
+            }
+            suf += __popc(S);
+            if (own) cache_add(S, c.x, peers, known);
+            if (!more) break;
+            ce = cb;
+            cb = nb;
+            c = nc;
+        }
+        __syncwarp();
+        if (lane == 0) {
+            ws.pos[k] = pos;
+            ws.end[k] = end;
+            ws.suf[k] = suf;
+            ws.mask[k] = 0;
+        }
+        __syncwarp();
+        const unsigned long long tot = warp_sum_u64(acc_l);
+        if (lane == 0) {
+            add_count(ref.counter, tot);
+            if (complete) {                              // Q_N: every survivor of the frame matches
+                for (int i = 0; i < N.n_ref; i++) {
+                    const DevRef r = p.tr.refs[N.ref_begin + i];
+                    if ((rmask >> r.query) & 1ull) add_count(r.counter, (unsigned long long)(suf - suf0));
+                }
+            }
+        }
+        return true;
+    }
+
     // A level whose survivors are only counted (nothing to descend): run all
     // its chunks, fetching the next chunk before filtering the current one.
     __device__ void drain(int k, int kbase) {
+        if (drain_star(k, kbase)) return;
         const int8_t lt = ws.ltype[k];
         int64_t base = chunk_base(k);
         int64_t end = ws.end[k];
