@@ -115,19 +115,13 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one timed mining
-# launch of the default benchmark, from a one-pass ncu capture of that launch,
-# keyed by a hash of the kernel source it was taken on and by the schedule of
-# the timed step; any other source reports null.  For 40f3baa3fc7c70a3, the
-# mean of the three timed launches of
-#   ncu --metrics gpu__time_duration.sum,dram__bytes_read.sum,dram__bytes_write.sum
-#       --clock-control none -c 3000 python bench.py --steps 3 --warmup 3
-#       --no-cpu-baseline --no-e2e --no-permotif
-# with the default plan and tunables (unit_work 1e6, max_split 4096,
-# poll_every 16, donate_leaf 4096): learned, 369.97 MB read + 38.97 MB written;
-# reactive (the three comparison launches of the same run), 461.2 MB read +
-# 59.4 MB written.
-TRAFFIC = {"40f3baa3fc7c70a3": {"learned": 408.9e6, "reactive": 520.6e6}}
+# Per-launch figures of the timed mining launch of the default benchmark from
+# one ncu capture of that launch (profiles/), keyed by a hash of the kernel
+# source they were taken on and by the schedule of the timed step; any other
+# source reports null.  dram_bytes = dram__bytes_read.sum +
+# dram__bytes_write.sum; l2_pct / dram_pct = ncu's L2 and DRAM throughput
+# (percent of peak sustained).
+PROFILE = {"3c73f3dbd24600e8": {"learned": {"dram_bytes": 420.9e6, "l2_pct": 10.4, "dram_pct": 0.012}}}
 
 
 def kernel_hash():
@@ -401,20 +395,35 @@ def run_serving(args):
 
 def run_probe(args):
     """One co-mining launch on the mid workload's first --roots sampled roots
-    (default 4): the small case the kernel profiles are taken on."""
+    (default 4): the small case the kernel profiles are taken on.  With
+    --probe-learned, the benchmark step's own launch: the cost model trained
+    as in the benchmark (two stats launches of k_mine), then features, plan
+    and the planned launch over the 64 benchmark roots."""
     import torch
     from paper_2507_14813_b300 import build, synth, tmotif
     build.build()
     src, dst, t = synth.make_graph(synth.MID)
     g = tmotif.Graph(src, dst, t, synth.MID.n_nodes, presorted=True)
     tr = tmotif.Tree(synth.CONFIG2_MOTIFS, synth.MID_DELTA)
-    r = torch.from_numpy(synth.root_sample(100, len(src), 64)[:args.roots or 4]).cuda()
+    n = 64 if args.probe_learned else (args.roots or 4)
+    r = torch.from_numpy(synth.root_sample(100, len(src), 64)[:n]).cuda()
     out = torch.zeros(len(synth.CONFIG2_MOTIFS), dtype=torch.int64, device="cuda")
-    t0 = time.perf_counter()
-    tmotif.tm_count(g.h, tr.h, roots=r, counts=out, mode=tmotif.TM_SCHED_DYNAMIC)
+    tune = {"ctas_per_sm": 0, "donate_seq": 0, "donate_leaf": args.donate_leaf, "poll_every": args.poll_every}
+    mode = tmotif.TM_SCHED_DYNAMIC
+    if args.probe_learned:
+        model, _ = train_cost_model(args, tmotif, g, tr, src, 0, r)
+        feats = torch.zeros((n, tmotif.TM_FEATURES), dtype=torch.float32, device="cuda")
+        ro, sp = torch.zeros_like(r), torch.zeros_like(r)
+        tmotif.tm_features(g.h, tr.h, r, feats)
+        model.plan(feats, r, ro, sp, unit_work=args.unit_work, max_split=args.max_split)
+        r, mode = ro, mode | tmotif.TM_SCHED_PLANNED
     torch.cuda.synchronize()
-    print(json.dumps({"probe": "mid, %d roots" % len(r), "counts": out.cpu().tolist(),
-                      "seconds": time.perf_counter() - t0}))
+    t0 = time.perf_counter()
+    tmotif.tm_count(g.h, tr.h, roots=r, counts=out, mode=mode, tune=tune,
+                    root_split=sp if args.probe_learned else None)
+    torch.cuda.synchronize()
+    print(json.dumps({"probe": "mid, %d roots%s" % (n, ", learned plan" if args.probe_learned else ""),
+                      "counts": out.cpu().tolist(), "seconds": time.perf_counter() - t0}))
     return 0
 
 
@@ -603,6 +612,8 @@ def main():
     ap.add_argument("--stress-rate", type=float, default=2000.0)
     ap.add_argument("--stress-duration", type=float, default=5.0)
     ap.add_argument("--mode", type=int, default=0, help="extra tm_count mode bits")
+    ap.add_argument("--probe-learned", action="store_true",
+                    help="probe workload: the benchmark step's planned launch over its 64 roots")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -757,7 +768,12 @@ def main():
                "d2h_bytes_per_step": 8 * n_m, "seconds_per_step": e2e_s}
 
     peak, peak_kind = measured_peaks()
-    achieved = st["algo_bytes"] / (ms_step / 1000.0) / 1e9
+    # algorithmic bytes per launch by list accounting: 16 per root, 8 per
+    # candidate scanned, 12 per binary-search step of each list opened
+    achieved = st["algo_bytes_lists"] / (ms_step / 1000.0) / 1e9
+    achieved_probes = st["algo_bytes"] / (ms_step / 1000.0) / 1e9
+    prof = PROFILE.get(kernel_hash(), {}).get("learned" if use_model else "reactive", {}) \
+        if args.workload == "mid" and len(roots) == 64 and not args.static else {}
     line = {
         "metric": "query root-edges/sec (roots x motifs / s), exact co-mining",
         "value": value, "unit": "root-edges/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -776,11 +792,19 @@ def main():
         "permotif_ms_per_step": perm,
         "comine_speedup_vs_permotif": (perm / ms_step) if perm else None,
         "permotif_reactive_ms_per_step": perm_reactive,
-        "work": {k: st[k] for k in ("candidates", "expansions", "probes", "leaf_evals", "algo_bytes", "warp_imbalance")},
+        "work": {k: st[k] for k in ("candidates", "expansions", "probes", "leaf_evals", "algo_bytes",
+                                     "algo_bytes_lists", "warp_imbalance", "idle_expired", "tasks_split")},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak,
-                     "traffic": (TRAFFIC.get(kernel_hash(), {}).get("learned" if use_model else "reactive")
-                                 if args.workload == "mid" and len(roots) == 64 and not args.static else None),
+                     "traffic": prof.get("dram_bytes"),
+                     "bytes_per_launch": st["algo_bytes_lists"],
+                     "accounting": "16 B per root + 8 B per candidate scanned + 12 B per binary-search step "
+                                   "(ceil(log2(len + 1))) of each candidate list opened",
+                     "achieved_probe_accounting": achieved_probes,
+                     "frac_probe_accounting": achieved_probes / peak,
+                     "probe_accounting": "16 B per root + 8 B per candidate + 8 B per list probe + 16 B per hash "
+                                         "probe + 4 B per pair-run probe",
+                     "l2_throughput_pct_ncu": prof.get("l2_pct"), "dram_throughput_pct_ncu": prof.get("dram_pct"),
                      "kernel": "k_mine", "kernel_source": kernel_hash(),
                      "peak_kind": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else peak_kind},
         "gpu_launches": (plan_launches(len(roots)) + 2 if use_model else 2) * args.steps,

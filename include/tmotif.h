@@ -181,6 +181,12 @@ typedef struct {
     double kernel_ms;         /* device time of the mining launches */
     double warp_imbalance;    /* max / mean over warps of busy cycles (time not spent waiting
                                  for work) in the stats launch: 1 is perfect balance */
+    int64_t algo_bytes_lists; /* bytes by list accounting: 16 per root + 8 per candidate scanned
+                                 + 12 * ceil(log2(len + 1)) per candidate list opened (an edge-id
+                                 and a time probe per binary-search step) */
+    int64_t idle_expired;     /* warps of the persistent launch whose bounded idle wait ran out
+                                 while other warps still held work (they left the launch early;
+                                 counts are unaffected) */
 } tm_run_stats;
 
 /*

@@ -89,7 +89,7 @@ struct QueueHdr {
     int idle;                 // warps waiting for work
     int busy;                 // warps holding work
     int error;                // kErr* bits
-    int pad;
+    int idle_expired;         // warps that left after their bounded idle wait ran out with work still held
 };
 
 struct Params {
@@ -117,7 +117,10 @@ struct Params {
     const uint64_t *root_qmask;       // per root index: queries it serves (bit q), or null = all
 };
 
-enum { kStCand = 0, kStExp, kStListProbe, kStHashProbe, kStPairProbe, kStLeaf, kStRoots, kStSplit, kStatFields };
+// kStLogDeg: sum over opened lists of ceil(log2(list length + 1)), the
+// probes a binary search of each list costs
+enum { kStCand = 0, kStExp, kStListProbe, kStHashProbe, kStPairProbe, kStLeaf, kStRoots, kStSplit, kStLogDeg,
+       kStatFields };
 // after the kStatFields totals: busy cycles of the busiest warp, their sum, and the warps
 enum { kBusyMax = 0, kBusySum, kBusyWarps, kBusyFields };
 
@@ -653,6 +656,7 @@ struct Miner {
         int32_t x;
         list_of(N, k, lt, x);
         int64_t start, end;
+        int64_t deg = p.g.E;                            // length of the list searched
         if (lt == kListGlobal) {
             start = (int64_t)last + 1;
             end = (int64_t)hi + 1;
@@ -660,6 +664,7 @@ struct Miner {
             const int64_t *off = lt == kListOut ? p.g.out_off : p.g.in_off;
             const int2 *adj = lt == kListOut ? p.g.out_adj : p.g.in_adj;
             const int64_t b0 = __ldg(off + x), b1 = __ldg(off + x + 1);
+            deg = b1 - b0;
             // the list of an endpoint of the previous match starts right after it (per-edge index)
             const int64_t ap = after_pos(p.g, lt == kListOut, x, last, ws.m2g[N.eu[k - 1]], ws.m2g[N.ev[k - 1]]);
             if (ap >= 0) start = ap;
@@ -676,7 +681,10 @@ struct Miner {
             if (lane == 0) ws.same_mode[k] = sm;
             __syncwarp();
         }
-        if (kStats && lane == 0) w.v[kStExp]++;
+        if (kStats && lane == 0) {
+            w.v[kStExp]++;
+            w.v[kStLogDeg] += (unsigned long long)(64 - __clzll((unsigned long long)deg));   // ceil(log2(deg + 1))
+        }
         if (k == 1 && split_h > 1) force_split(k, split_h);
     }
 
@@ -806,6 +814,7 @@ struct Miner {
         if (lane == 0) {
             atomicSub(&p.q->busy, 1);
             atomicAdd(&p.q->idle, 1);
+            bool done = false;
             for (long long it = 0; it < kIdleSpins; it++) {
                 unsigned int h = vloadu(&p.q->head);
                 unsigned int t = min(vloadu(&p.q->tail), (unsigned int)kQueueCap);
@@ -818,10 +827,13 @@ struct Miner {
                     __threadfence();
                     h = vloadu(&p.q->head);
                     t = min(vloadu(&p.q->tail), (unsigned int)kQueueCap);
-                    if (h >= t) break;                   // nothing queued, nobody working: done
+                    if (h >= t) { done = true; break; }  // nothing queued, nobody working: done
                 }
                 __nanosleep(256);
             }
+            // the wait ran out while other warps still held work: this warp
+            // leaves (their work stays theirs, so counts are unaffected)
+            if (!r && !done) atomicAdd(&p.q->idle_expired, 1);
             atomicSub(&p.q->idle, 1);
         }
         return __shfl_sync(0xffffffffu, r, 0) != 0;
@@ -1561,6 +1573,7 @@ int mine(const tm_graph *g, const tm_tree *tr, const tm_count_args *args, int64_
     // error bits (expired waits, skipped device roots) come back with the
     // queue headers whenever the call synchronises anyway; the dynamic mode
     // always synchronises for them
+    int64_t idle_expired = 0;
     if (P.dynamic || !dev_counts || stats) {
         std::vector<QueueHdr> hq(P.n_launch);
         cudaMemcpyAsync(hq.data(), scratch + P.o_q, sizeof(QueueHdr) * P.n_launch, cudaMemcpyDeviceToHost, s);
@@ -1570,6 +1583,7 @@ int mine(const tm_graph *g, const tm_tree *tr, const tm_count_args *args, int64_
             return finish(TM_ECUDA);
         }
         for (auto &q : hq) {
+            idle_expired += q.idle_expired;
             if (q.error & kErrTimeout) {
                 set_error("tm_count: a bounded device wait expired; counts are incomplete");
                 return finish(TM_ETIMEOUT);
@@ -1612,6 +1626,8 @@ int mine(const tm_graph *g, const tm_tree *tr, const tm_count_args *args, int64_
         stats->algo_bytes = (int64_t)(16 * hs[kStRoots] + 8 * hs[kStCand] + 8 * hs[kStListProbe] +
                                       16 * hs[kStHashProbe] + 4 * hs[kStPairProbe]);
         stats->tasks_split = (int64_t)hs[kStSplit];
+        stats->algo_bytes_lists = (int64_t)(16 * hs[kStRoots] + 8 * hs[kStCand] + 12 * hs[kStLogDeg]);
+        stats->idle_expired = idle_expired;
         const unsigned long long *hb = hs + kStatFields;
         stats->warp_imbalance = hb[kBusySum] ? (double)hb[kBusyMax] * (double)hb[kBusyWarps] / (double)hb[kBusySum] : 0.0;
         stats->launches = launches;

@@ -114,7 +114,8 @@ class tm_run_stats(ctypes.Structure):
     _fields_ = [("n_roots", ctypes.c_int64), ("candidates", ctypes.c_int64), ("expansions", ctypes.c_int64),
                 ("probes", ctypes.c_int64), ("leaf_evals", ctypes.c_int64), ("algo_bytes", ctypes.c_int64),
                 ("tasks_split", ctypes.c_int64), ("launches", ctypes.c_int64), ("kernel_ms", ctypes.c_double),
-                ("warp_imbalance", ctypes.c_double)]
+                ("warp_imbalance", ctypes.c_double), ("algo_bytes_lists", ctypes.c_int64),
+                ("idle_expired", ctypes.c_int64)]
 
     def as_dict(self):
         return {name: getattr(self, name) for name, _ in self._fields_}

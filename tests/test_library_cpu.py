@@ -130,3 +130,27 @@ def test_auto_mode_and_threshold_are_declared():
     assert "#define TM_COMINE_MIN_SM 0.44" in txt and tmotif.TM_COMINE_MIN_SM == 0.44
     # one match record: motif, n_edges, TM_MAX_EDGES edge ids, all int32
     assert tmotif.MATCH_FIELDS == 2 + tmotif.TM_MAX_EDGES
+
+
+def test_binding_struct_layouts_match_the_header(tmp_path):
+    """Every struct the binding mirrors has the size and field offsets the C
+    header gives it (compiled with the host compiler)."""
+    import subprocess
+    structs = [tmotif.tm_graph_info, tmotif.tm_tree_info, tmotif.tm_tree_node, tmotif.tm_count_args,
+               tmotif.tm_server_config, tmotif.tm_request_stats, tmotif.tm_server_info, tmotif.tm_tune,
+               tmotif.tm_run_stats]
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "tmotif.h"', "int main(void) {"]
+    for st in structs:
+        lines.append('printf("%s %%zu\\n", sizeof(%s));' % (st.__name__, st.__name__))
+        for name, _ in st._fields_:
+            lines.append('printf("%s.%s %%zu\\n", offsetof(%s, %s));' % (st.__name__, name, st.__name__, name))
+    lines.append("return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), "-o", str(exe), str(src)])
+    got = dict(line.split() for line in subprocess.check_output([str(exe)]).decode().splitlines())
+    for st in structs:
+        assert int(got[st.__name__]) == ctypes.sizeof(st), st.__name__
+        for name, _ in st._fields_:
+            assert int(got["%s.%s" % (st.__name__, name)]) == getattr(st, name).offset, (st.__name__, name)
