@@ -125,9 +125,12 @@ PROFILE = {"3c73f3dbd24600e8": {"learned": {"dram_bytes": 420.9e6, "l2_pct": 10.
 
 
 def kernel_hash():
+    """Hash of the mining kernel's sources (the kernel and the device types)."""
     import hashlib
-    p = os.path.join(ROOT, "paper_2507_14813_b300", "csrc", "tm_mine.cu")
-    return hashlib.sha256(open(p, "rb").read()).hexdigest()[:16]
+    h = hashlib.sha256()
+    for name in ("tm_kernel.cuh", "tm_device.h"):
+        h.update(open(os.path.join(ROOT, "paper_2507_14813_b300", "csrc", name), "rb").read())
+    return h.hexdigest()[:16]
 
 
 def measured_peaks():
@@ -405,6 +408,8 @@ def run_probe(args):
     src, dst, t = synth.make_graph(synth.MID)
     g = tmotif.Graph(src, dst, t, synth.MID.n_nodes, presorted=True)
     tr = tmotif.Tree(synth.CONFIG2_MOTIFS, synth.MID_DELTA)
+    if not args.generic:
+        tr.compile()
     n = 64 if args.probe_learned else (args.roots or 4)
     r = torch.from_numpy(synth.root_sample(100, len(src), 64)[:n]).cuda()
     out = torch.zeros(len(synth.CONFIG2_MOTIFS), dtype=torch.int64, device="cuda")
@@ -595,6 +600,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-permotif", action="store_true")
     ap.add_argument("--static", action="store_true", help="one warp per root, no subtree splitting")
+    ap.add_argument("--generic", action="store_true", help="the table-driven kernel only (no code generation)")
     ap.add_argument("--no-learned", action="store_true")
     ap.add_argument("--train-roots", type=int, default=512)
     ap.add_argument("--unit-work", type=float, default=1e6)
@@ -641,11 +647,19 @@ def main():
     n_m = len(motifs)
     g = tmotif.Graph(src, dst, t, spec.n_nodes, presorted=True)
     tr = tmotif.Tree(motifs, delta)
+    # kernels specialised to the tree and to each motif's chain (runtime code
+    # generation), compiled before any timed region like the tree itself
+    codegen = None
+    if not args.generic:
+        t0 = time.perf_counter()
+        codegen = tr.compile(0 if args.no_permotif else tmotif.TM_COMPILE_CHAINS)
+        codegen["seconds"] = time.perf_counter() - t0
     d_roots = torch.from_numpy(roots).cuda()
     counts = torch.zeros(n_m, dtype=torch.int64, device="cuda")
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
-    mode = tmotif.TM_COMINE | args.mode | (0 if args.static else tmotif.TM_SCHED_DYNAMIC)
+    mode = tmotif.TM_COMINE | args.mode | (0 if args.static else tmotif.TM_SCHED_DYNAMIC) | \
+        (tmotif.TM_GENERIC if args.generic else 0)
     # learned scheduling (a11, a12): the model is trained before the timed
     # region; every step computes features, predicts, plans and counts
     model, learned = None, None
@@ -727,6 +741,8 @@ def main():
 
     # the same step without the model: reactive splitting alone
     reactive = timed(mode, False, n_cmp) if use_model else None
+    # the same step with the table-driven kernel in place of the tree's own
+    generic = timed(mode | tmotif.TM_GENERIC, use_model, n_cmp) if codegen else None
 
     # per-motif comparator on the same roots (one chain tree per motif), same schedule
     perm = perm_reactive = None
@@ -748,6 +764,8 @@ def main():
             t0 = time.perf_counter()
             g2 = tmotif.Graph(src, dst, t, spec.n_nodes, presorted=True)
             tr2 = tmotif.Tree(motifs, delta)
+            if codegen:
+                tr2.compile()                   # the process cache holds this tree's program
             if use_model:
                 r2 = torch.from_numpy(h_roots).cuda()
                 f2 = torch.empty((R, tmotif.TM_FEATURES), dtype=torch.float32, device="cuda")
@@ -789,6 +807,10 @@ def main():
                      "donate_leaf": args.donate_leaf},
         "reactive_ms_per_step": reactive,
         "learned_speedup_vs_reactive": (reactive / ms_step) if reactive else None,
+        "kernel": ("specialised to the tree (runtime code generation)" if codegen else "table-driven"),
+        "codegen": codegen,
+        "generic_ms_per_step": generic,
+        "specialised_speedup_vs_generic": (generic / ms_step) if generic else None,
         "permotif_ms_per_step": perm,
         "comine_speedup_vs_permotif": (perm / ms_step) if perm else None,
         "permotif_reactive_ms_per_step": perm_reactive,

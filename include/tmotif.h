@@ -37,6 +37,8 @@ extern "C" {
 #define TM_ECUDA (-3)         /* a CUDA call failed */
 #define TM_ETIMEOUT (-4)      /* a bounded device-side wait ran out */
 #define TM_EUNSUPPORTED (-5)  /* motif beyond TM_MAX_EDGES / TM_MAX_VERTICES */
+#define TM_ECHECK (-6)        /* the checking build (TM_CHECK) found an index outside its range:
+                                 an internal error of the library; counts are incomplete */
 
 /* ------------------------------------------------------------ limits */
 #define TM_MAX_EDGES 8        /* edges per motif */
@@ -112,6 +114,8 @@ typedef struct {
     int32_t n_deltas;         /* distinct windows */
     int32_t max_vertices;
     double similarity;        /* SM of Section 6: 1 - sum(|E_N|-|E_parent|) / sum |E_M| */
+    int32_t specialized;      /* kernels compiled for this tree (tm_tree_compile): 0, 1 + chains */
+    int32_t reserved;
 } tm_tree_info;
 
 int tm_tree_get_info(const tm_tree *tr, tm_tree_info *info);
@@ -130,6 +134,47 @@ int tm_tree_get_node(const tm_tree *tr, int32_t index, tm_tree_node *node);
 
 int tm_tree_free(tm_tree *tr);
 
+/* ------------------------------------------------------------ code generation */
+/*
+ * Compile mining kernels specialised to this tree (Section 5.1, "GPU
+ * Code-generation": the paper generates a kernel per motif group so that the
+ * matching order, the mapped-vertex checks and the counters of each node are
+ * fixed in the code).  The library compiles its own kernel source at run time
+ * (NVRTC, sm_103a) behind a generated prelude: the node, ref and window
+ * tables become constant data of the kernel, the tree's depth and vertex
+ * count size every per-level array and mapped-label loop (and so the
+ * registers and shared memory), and the window and counter counts are
+ * compile-time constants.  Afterwards tm_count uses the specialised kernel
+ * for this tree whenever mode has neither TM_LEAF_SCAN nor TM_GENERIC; the
+ * counts are those of the table-driven kernel.
+ *   flags: TM_COMPILE_CHAINS also compiles one kernel per distinct motif, used
+ *          by TM_PERMOTIF
+ *   info:  optional, filled on success
+ * Kernels are cached for the life of the process by their generated program,
+ * so trees of the same shape and windows compile once.  Compilation takes
+ * seconds; call it before timing or capturing counts, not inside a stream
+ * capture.  Not thread-safe against tm_count on the same tree.  Errors:
+ * TM_EINVAL (NULL tree, unknown flag), TM_EUNSUPPORTED (more than
+ * TM_SPEC_MAX_NODES nodes: such trees keep the table-driven kernel), TM_ECUDA
+ * (the runtime compiler or loader failed; tm_last_error has its log).
+ */
+#define TM_COMPILE_CHAINS 0x1u
+#define TM_COMPILE_CHECK 0x2u   /* compile only (no device needed): the tree keeps its kernels */
+#define TM_SPEC_MAX_NODES 256
+
+typedef struct {
+    int32_t kernels;          /* programs the tree now has */
+    int32_t compiled;         /* of them compiled by this call; the rest came from the cache */
+    double wall_ms;           /* wall time of the call */
+    int32_t registers;        /* per thread, MG-Tree kernel (counting launch) */
+    int32_t local_bytes;      /* local memory per thread (register spills), same kernel */
+    int32_t static_smem;      /* static shared memory per CTA, same kernel */
+    int32_t reserved;
+    uint64_t source_hash;     /* FNV-1a of that kernel's generated program */
+} tm_compile_info;
+
+int tm_tree_compile(tm_tree *tr, uint32_t flags, tm_compile_info *info);
+
 /* ------------------------------------------------------------ counting */
 /* mode bits */
 #define TM_COMINE 0x0u        /* walk the MG-Tree (Algorithm 3) */
@@ -138,6 +183,7 @@ int tm_tree_free(tm_tree *tr);
 #define TM_LEAF_SCAN 0x10u    /* count a leaf's last edge by scanning its window only */
 #define TM_SCHED_DYNAMIC 0x100u /* persistent launch, heavy subtrees split across warps */
 #define TM_SCHED_PLANNED 0x200u /* persistent launch; cut root i's first-level lists into root_split[i] slices */
+#define TM_GENERIC 0x1000u    /* the table-driven kernel even when the tree has a specialised one */
 
 /* flags */
 #define TM_ROOTS_DEVICE 0x1u  /* roots points to device memory */

@@ -6,6 +6,7 @@
 #include <cstring>
 #include <string>
 
+#include "tm_codegen.h"
 #include "tm_internal.h"
 
 namespace tmo {
@@ -85,6 +86,8 @@ int tm_tree_get_info(const tm_tree *tr, tm_tree_info *info) {
     info->n_deltas = tr->h.n_deltas;
     info->max_vertices = tr->h.max_vertices;
     info->similarity = tr->h.similarity;
+    info->specialized = (spec_kernel(tr, 0) ? 1 : 0);
+    for (int i = 0; i < (int)tr->chains.size(); i++) info->specialized += spec_kernel(tr, 1 + i) ? 1 : 0;
     return TM_OK;
 }
 
@@ -111,11 +114,18 @@ int tm_tree_free(tm_tree *tr) {
     return TM_OK;
 }
 
+int tm_tree_compile(tm_tree *tr, uint32_t flags, tm_compile_info *info) {
+    g_last_error.clear();
+    if (!tr) { set_error("tm_tree_compile: NULL tree"); return TM_EINVAL; }
+    if (flags & ~(TM_COMPILE_CHAINS | TM_COMPILE_CHECK)) { set_error("tm_tree_compile: unknown flag"); return TM_EINVAL; }
+    return tree_compile(tr, flags, info);
+}
+
 int tm_count(const tm_graph *g, const tm_tree *tr, const tm_count_args *args, int64_t *counts, tm_run_stats *stats,
              void *stream) {
     g_last_error.clear();
     if (!g || !tr || !args || !counts) { set_error("tm_count: NULL argument"); return TM_EINVAL; }
-    if (args->mode & ~(TM_PERMOTIF | TM_AUTO | TM_LEAF_SCAN | TM_SCHED_DYNAMIC | TM_SCHED_PLANNED)) {
+    if (args->mode & ~(TM_PERMOTIF | TM_AUTO | TM_LEAF_SCAN | TM_SCHED_DYNAMIC | TM_SCHED_PLANNED | TM_GENERIC)) {
         set_error("tm_count: unknown mode bit");
         return TM_EINVAL;
     }

@@ -23,6 +23,7 @@ TM_ENOMEM = -2
 TM_ECUDA = -3
 TM_ETIMEOUT = -4
 TM_EUNSUPPORTED = -5
+TM_ECHECK = -6
 TM_MAX_EDGES = 8
 TM_MAX_VERTICES = 8
 
@@ -36,6 +37,10 @@ TM_COMINE_MIN_SM = 0.44
 TM_LEAF_SCAN = 0x10
 TM_SCHED_DYNAMIC = 0x100
 TM_SCHED_PLANNED = 0x200
+TM_GENERIC = 0x1000
+TM_COMPILE_CHAINS = 0x1
+TM_COMPILE_CHECK = 0x2
+TM_SPEC_MAX_NODES = 256
 TM_FEATURES = 8
 TM_MODEL_PARAMS = 4801
 
@@ -50,7 +55,7 @@ TM_WORK_FIELDS = 4
 WORK_NAMES = ("candidates", "expansions", "probes", "leaf_evals")
 
 ERRORS = {TM_EINVAL: "TM_EINVAL", TM_ENOMEM: "TM_ENOMEM", TM_ECUDA: "TM_ECUDA",
-          TM_ETIMEOUT: "TM_ETIMEOUT", TM_EUNSUPPORTED: "TM_EUNSUPPORTED"}
+          TM_ETIMEOUT: "TM_ETIMEOUT", TM_EUNSUPPORTED: "TM_EUNSUPPORTED", TM_ECHECK: "TM_ECHECK"}
 
 
 class TMError(RuntimeError):
@@ -68,7 +73,7 @@ class tm_graph_info(ctypes.Structure):
 class tm_tree_info(ctypes.Structure):
     _fields_ = [("n_motifs", ctypes.c_int32), ("n_nodes", ctypes.c_int32), ("n_leaves", ctypes.c_int32),
                 ("depth", ctypes.c_int32), ("n_deltas", ctypes.c_int32), ("max_vertices", ctypes.c_int32),
-                ("similarity", ctypes.c_double)]
+                ("similarity", ctypes.c_double), ("specialized", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class tm_tree_node(ctypes.Structure):
@@ -110,6 +115,15 @@ class tm_tune(ctypes.Structure):
         return {name: getattr(self, name) for name, _ in self._fields_}
 
 
+class tm_compile_info(ctypes.Structure):
+    _fields_ = [("kernels", ctypes.c_int32), ("compiled", ctypes.c_int32), ("wall_ms", ctypes.c_double),
+                ("registers", ctypes.c_int32), ("local_bytes", ctypes.c_int32), ("static_smem", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("source_hash", ctypes.c_uint64)]
+
+    def as_dict(self):
+        return {name: getattr(self, name) for name, _ in self._fields_ if name != "reserved"}
+
+
 class tm_run_stats(ctypes.Structure):
     _fields_ = [("n_roots", ctypes.c_int64), ("candidates", ctypes.c_int64), ("expansions", ctypes.c_int64),
                 ("probes", ctypes.c_int64), ("leaf_evals", ctypes.c_int64), ("algo_bytes", ctypes.c_int64),
@@ -124,7 +138,7 @@ class tm_run_stats(ctypes.Structure):
 _lib = None
 
 EXPORTS = ("tm_graph_load", "tm_graph_get_info", "tm_graph_edges", "tm_graph_free", "tm_tree_build",
-           "tm_tree_get_info", "tm_tree_get_node", "tm_tree_free", "tm_count", "tm_count_noalloc",
+           "tm_tree_get_info", "tm_tree_get_node", "tm_tree_free", "tm_tree_compile", "tm_count", "tm_count_noalloc",
            "tm_graph_bipartite", "tm_comine_advice", "tm_enumerate",
            "tm_features", "tm_model_create", "tm_model_free", "tm_model_get_params", "tm_model_set_params",
            "tm_model_fit_norm", "tm_model_predict", "tm_model_loss_grad", "tm_model_train", "tm_plan",
@@ -149,6 +163,7 @@ def lib():
         L.tm_tree_get_info.argtypes = [P, ctypes.POINTER(tm_tree_info)]
         L.tm_tree_get_node.argtypes = [P, i32, ctypes.POINTER(tm_tree_node)]
         L.tm_tree_free.argtypes = [P]
+        L.tm_tree_compile.argtypes = [P, u32, ctypes.POINTER(tm_compile_info)]
         L.tm_count.argtypes = [P, P, ctypes.POINTER(tm_count_args), P, ctypes.POINTER(tm_run_stats), P]
         L.tm_count_noalloc.argtypes = [P, P, P, i64, i64, i64, P, P]
         F = ctypes.c_float
@@ -289,7 +304,7 @@ def tm_tree_build(motifs: Sequence, deltas) -> ctypes.c_void_p:
 def tm_tree_get_info(tr) -> dict:
     info = tm_tree_info()
     _check(lib().tm_tree_get_info(tr, ctypes.byref(info)))
-    return {name: getattr(info, name) for name, _ in info._fields_}
+    return {name: getattr(info, name) for name, _ in info._fields_ if name != "reserved"}
 
 
 def tm_tree_get_node(tr, index: int) -> dict:
@@ -301,6 +316,14 @@ def tm_tree_get_node(tr, index: int) -> dict:
 
 def tm_tree_free(tr) -> None:
     _check(lib().tm_tree_free(tr))
+
+
+def tm_tree_compile(tr, flags: int = 0) -> dict:
+    """Compile kernels specialised to the tree (runtime code generation);
+    later counts on it use them unless mode has TM_GENERIC or TM_LEAF_SCAN."""
+    info = tm_compile_info()
+    _check(lib().tm_tree_compile(tr, int(flags), ctypes.byref(info)))
+    return info.as_dict()
 
 
 def _count_args(mode=TM_COMINE, roots=None, root_lo=0, root_hi=0, per_root_counts=None, per_root_work=None,
@@ -631,6 +654,9 @@ class Tree:
 
     def node(self, i: int) -> dict:
         return tm_tree_get_node(self.h, i)
+
+    def compile(self, flags: int = 0) -> dict:
+        return tm_tree_compile(self.h, flags)
 
     def nodes(self):
         return [self.node(i) for i in range(self.info()["n_nodes"])]
