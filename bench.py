@@ -291,9 +291,26 @@ def run_batched(args):
         seq_ms = a.elapsed_time(b)
         if not torch.equal(torch.cat(outs), ref):
             raise SystemExit("per-set counts differ from the batched launch")
+    # the paper's sibling splitting and multi-offload in place of halving slices
+    sib_ms = None
+    if not args.no_permotif:
+        S = tmotif.TM_SCHED_SIBLINGS
+        tmotif.tm_count(g.h, tr.h, mode=S, roots=roots, counts=counts, tune=tune)
+        ts = []
+        for i in range(3):
+            flush.fill_(i & 0xFF)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            tmotif.tm_count(g.h, tr.h, mode=S, roots=roots, counts=counts, stream=stream, tune=tune)
+            b.record(stream)
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b))
+        if not torch.equal(counts, ref):
+            raise SystemExit("sibling-split counts differ from the batched launch")
+        sib_ms = statistics.median(ts)
     _, st = tmotif.tm_count(g.h, tr.h, mode=D, roots=roots, stats=True, tune=tune)
     peak, peak_kind = measured_peaks()
-    achieved = st["algo_bytes"] / (ms / 1000.0) / 1e9
+    achieved = st["algo_bytes_lists"] / (ms / 1000.0) / 1e9
     line = {
         "metric": "query root-edges/sec (roots x motifs / s), 64 motif sets in one batched launch",
         "value": R * len(motifs) / (ms / 1000.0), "unit": "root-edges/s", "n_gpus": world, "steps": args.steps,
@@ -303,7 +320,7 @@ def run_batched(args):
                                "(%d motifs of 2-6 edges, windows 600/3600/86400 s) merged into one tree; %d roots"
                                % (spec.name, spec.n_nodes, spec.n_edges, spec.zipf_s, len(motifs), R),
                    "l2": "flushed between steps (256 MiB write)", "launch": "CUDA graph replay of one persistent launch"},
-        "tree": tr.info(), "autotune": tune, "sets_one_by_one_ms": seq_ms,
+        "tree": tr.info(), "autotune": tune, "sets_one_by_one_ms": seq_ms, "siblings_ms": sib_ms,
         "batched_speedup_vs_one_by_one": (seq_ms / ms) if seq_ms else None,
         "work": {k: st[k] for k in ("candidates", "probes", "leaf_evals", "tasks_split", "algo_bytes", "warp_imbalance")},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
@@ -743,6 +760,9 @@ def main():
     reactive = timed(mode, False, n_cmp) if use_model else None
     # the same step with the table-driven kernel in place of the tree's own
     generic = timed(mode | tmotif.TM_GENERIC, use_model, n_cmp) if codegen else None
+    # the same step with the paper's sibling splitting and multi-offload in
+    # place of halving slices for idle warps
+    siblings = timed(mode | tmotif.TM_SCHED_SIBLINGS, use_model, n_cmp) if not args.static else None
 
     # per-motif comparator on the same roots (one chain tree per motif), same schedule
     perm = perm_reactive = None
@@ -811,6 +831,8 @@ def main():
         "codegen": codegen,
         "generic_ms_per_step": generic,
         "specialised_speedup_vs_generic": (generic / ms_step) if generic else None,
+        "siblings_ms_per_step": siblings,
+        "schedule_siblings": "the same step with sibling splitting and multi-offload (TM_SCHED_SIBLINGS)",
         "permotif_ms_per_step": perm,
         "comine_speedup_vs_permotif": (perm / ms_step) if perm else None,
         "permotif_reactive_ms_per_step": perm_reactive,

@@ -184,6 +184,10 @@ int tm_tree_compile(tm_tree *tr, uint32_t flags, tm_compile_info *info);
 #define TM_SCHED_DYNAMIC 0x100u /* persistent launch, heavy subtrees split across warps */
 #define TM_SCHED_PLANNED 0x200u /* persistent launch; cut root i's first-level lists into root_split[i] slices */
 #define TM_GENERIC 0x1000u    /* the table-driven kernel even when the tree has a specialised one */
+#define TM_SCHED_SIBLINGS 0x400u /* TM_SCHED_DYNAMIC with the paper's sibling splitting (a warp about to
+                                    descend into several children hands all but the first to idle
+                                    warps as separate tasks) and multi-offload (a donation hands
+                                    over up to one piece per idle warp, at most offload_max) */
 
 /* flags */
 #define TM_ROOTS_DEVICE 0x1u  /* roots points to device memory */
@@ -206,12 +210,12 @@ typedef struct {
     int64_t *per_root_counts; /* device, [n_roots][n_motifs], or NULL; overwritten */
     int64_t *per_root_work;   /* device, [n_roots][TM_WORK_FIELDS], or NULL; overwritten */
     int32_t ctas_per_sm;      /* 0: library default */
-    int32_t reserved;
+    int32_t offload_max;      /* TM_SCHED_SIBLINGS: most pieces one donation hands over (0: default 8) */
     const int32_t *root_split; /* device, per root: slices for TM_SCHED_PLANNED (<= 1: none), or NULL */
     int32_t poll_every;       /* TM_SCHED_DYNAMIC: chunk loads between looks for idle warps (0: default 4) */
     int32_t donate_seq;       /* min unscanned entries to split a level that descends (0: default 64) */
     int32_t donate_leaf;      /* ... a level whose survivors are only counted (0: default 1024) */
-    int32_t reserved2;
+    int32_t sibling_always;   /* TM_SCHED_SIBLINGS: split siblings even when no warp is idle (tests) */
 } tm_count_args;
 
 typedef struct {

@@ -107,6 +107,7 @@ constexpr int kQueueCap = 1 << 20;        // tasks per launch (slots are not reu
 constexpr int kPollEvery = 4;             // default: chunk loads between looks at the idle counter
 constexpr int kDonateSeq = 64;            // default: min unscanned entries to split a level that descends
 constexpr int kDonateLeaf = 1024;         // default: ... a level whose survivors are only counted
+constexpr int kOffloadMax = 8;            // default: most pieces one multi-offload hands over
 #ifdef TM_TEST_READY_SPINS
 constexpr long long kReadySpins = TM_TEST_READY_SPINS;
 #else
@@ -117,7 +118,9 @@ constexpr long long kIdleSpins = 1 << 20;   // bound on an idle warp's wait for 
 enum : int8_t { kListOut = 0, kListIn = 1, kListGlobal = 2 };
 
 // A unit of work: the slice [lo, hi) of level k's candidate list of `node`,
-// under the partial match eid[0..k-1] (eid[0] is the root edge).
+// under the partial match eid[0..k-1] (eid[0] is the root edge).  lo < 0
+// marks a sibling task: open `node` at level k afresh (its whole list) and
+// mine that node's subtree only.
 struct __align__(16) Task {
     int32_t ri;               // root index, for per-root outputs
     int16_t node;
@@ -164,7 +167,9 @@ struct Params {
     int32_t poll_every;               // chunk loads between looks at the idle counter
     int32_t donate_seq;               // min unscanned entries to split a level that descends
     int32_t donate_leaf;              // ... a level whose survivors are only counted
-    int32_t pad2;
+    int32_t siblings;                 // 1: sibling splitting and multi-offload (TM_SCHED_SIBLINGS)
+    int32_t sib_always;               // 1: split siblings even when no warp is idle
+    int32_t offload_max;              // most pieces one donation hands over (multi-offload)
     const uint64_t *root_qmask;       // per root index: queries it serves (bit q), or null = all
 };
 
@@ -813,6 +818,87 @@ struct Miner {
         return true;
     }
 
+    // Sibling splitting (the paper's GPU load balancing): the children
+    // [first + 1, end) of the current partial match go to the queue as one
+    // task each, when warps are idle (or always, for tests); returns the end
+    // of the children this warp keeps (first + 1 when every push succeeded).
+    __device__ int split_siblings(int k, int first, int end) {
+        int idle = 0;
+        if (lane == 0 && !p.sib_always) idle = vload(&p.q->idle);
+        idle = __shfl_sync(0xffffffffu, idle, 0);
+        if (!p.sib_always && idle <= 0) return end;
+        for (int c = end - 1; c > first; c--) {      // the last child first: the warp keeps a prefix
+            if (!push_task_node(k, c)) return c + 1;
+            end = c;
+        }
+        return end;
+    }
+
+    // Publish "open node `node` at level k" under the current partial match.
+    __device__ bool push_task_node(int k, int node) {
+        unsigned int slot = 0;
+        if (lane == 0) slot = atomicAdd(&p.q->tail, 1u);
+        slot = __shfl_sync(0xffffffffu, slot, 0);
+        if (slot >= (unsigned int)kQueueCap) return false;
+        Task *tk = p.tasks + slot;
+        if (lane < kMaxE) tk->eid[lane] = lane < k ? ws.eid[lane] : -1;
+        if (lane == 0) {
+            tk->ri = (int32_t)ri;
+            tk->node = (int16_t)node;
+            tk->k = (int8_t)k;
+            tk->lo = -1;
+            tk->hi = -1;
+            tk->wend = 0;
+        }
+        __threadfence();
+        __syncwarp();
+        if (lane == 0) {
+            __threadfence();
+            for (int i = 0; i < TM_TEST_PUBLISH_PAUSE; i++) __nanosleep(1000);
+            atomicExch(p.ready + slot, 1);
+        }
+        if (kStats && lane == 0) w.v[kStSplit]++;
+        __syncwarp();
+        return true;
+    }
+
+    // Multi-offload: hand up to min(idle warps, offload_max) pieces of whole
+    // chunks of level kb's unscanned slice to the queue at once, keeping one
+    // piece; returns false when nothing was handed over.
+    __device__ bool offload(int kb, int idle) {
+        const int64_t pos = ws.pos[kb], end = ws.end[kb];
+        const int64_t rem = end - pos;
+        const int64_t minsz = ws.seq[kb] ? p.donate_seq : p.donate_leaf;
+        int pieces = min(idle, p.offload_max);
+        pieces = (int)min((int64_t)pieces, rem / max(minsz, (int64_t)32) - 1);
+        if (pieces < 1) pieces = 1;
+        const int64_t sz = ((rem + pieces) / (pieces + 1) + 31) & ~31ll;
+        if (ws.star[kb]) {                           // scanned top-down: keep the top piece
+            const int64_t keep = max(pos, end - sz);
+            int64_t cur = pos;
+            for (int i = 0; i < pieces && cur < keep; i++) {
+                const int64_t hi = min(keep, cur + sz);
+                if (!push_task(kb, cur, hi)) break;
+                cur = hi;
+            }
+            __syncwarp();
+            if (lane == 0) ws.pos[kb] = cur;
+            __syncwarp();
+            return cur > pos;
+        }
+        const int64_t keep = min(end, pos + sz);      // keep the bottom piece
+        int64_t cur = end;
+        for (int i = 0; i < pieces && cur > keep; i++) {
+            const int64_t lo = max(keep, cur - sz);
+            if (!push_task(kb, lo, cur)) break;
+            cur = lo;
+        }
+        __syncwarp();
+        if (lane == 0) ws.end[kb] = cur;
+        __syncwarp();
+        return cur < end;
+    }
+
     // Hand [mid, end) of the shallowest long slice in levels [kbase, top] to the queue.
     __device__ void maybe_donate(int kbase, int top) {
         int idle = 0;
@@ -828,6 +914,10 @@ struct Miner {
             const int64_t pos = ws.pos[kb], end = ws.end[kb];
             const int64_t rem = end - pos;
             if (rem < (ws.seq[kb] ? p.donate_seq : p.donate_leaf)) continue;
+            if (p.siblings) {                          // multi-offload
+                offload(kb, idle);
+                return;
+            }
             const int64_t mid = pos + (((rem >> 1) + 31) & ~31ll);
             if (ws.star[kb]) {                         // scanned top-down: hand over the bottom part
                 if (push_task(kb, pos, mid)) {
@@ -1223,7 +1313,9 @@ struct Miner {
                 // (the checking build: no frame beyond the deepest level)
                 if (k == N.k_end - 1) {
                     if (N.n_seq > 0 && chk(k + 1 < kMaxE)) {
-                        open(k + 1, N.child_begin, N.child_begin + N.n_seq);
+                        int sib_end = N.child_begin + N.n_seq;
+                        if (p.siblings && N.n_seq > 1) sib_end = split_siblings(k + 1, N.child_begin, sib_end);
+                        open(k + 1, N.child_begin, sib_end);
                         k++;
                     }
                 } else if (chk(k + 1 < kMaxE)) {
@@ -1292,6 +1384,13 @@ struct Miner {
             }
         }
         __syncwarp();
+        if (tk.lo < 0) {                               // a sibling task: this node's subtree alone
+            if (lane == 0) ws.cache_owner = -1;
+            __syncwarp();
+            open(k, tk.node, tk.node + 1);
+            run(k);
+            return;
+        }
         int8_t lt;
         int32_t x;
         list_of(N, k, lt, x);

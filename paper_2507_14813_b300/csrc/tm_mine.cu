@@ -42,6 +42,7 @@ struct Plan {
     int n_motifs = 0, n_launch = 0;
     bool comine = true, par = true, react = false, planned = false, dynamic = false, stats = false;
     bool spec = false;                  // counting launches may use the tree's specialised kernels
+    bool siblings = false;              // sibling splitting and multi-offload
     int64_t n_roots = 0, root_lo = 0;
     const int32_t *roots = nullptr;     // device
     const uint64_t *root_qmask = nullptr; // device, serving batches only
@@ -62,7 +63,8 @@ int make_plan(const tm_graph *g, const tm_tree *tr, const tm_count_args *args, b
     P->n_motifs = tr->h.n_motifs;
     P->comine = (args->mode & TM_PERMOTIF) == 0;
     P->par = (args->mode & TM_LEAF_SCAN) == 0;
-    P->react = (args->mode & TM_SCHED_DYNAMIC) != 0;
+    P->siblings = (args->mode & TM_SCHED_SIBLINGS) != 0;
+    P->react = (args->mode & (TM_SCHED_DYNAMIC | TM_SCHED_SIBLINGS)) != 0;
     P->planned = (args->mode & TM_SCHED_PLANNED) != 0;
     P->dynamic = P->react || P->planned;
     P->stats = stats;
@@ -176,7 +178,9 @@ int enqueue(const tm_graph *g, const tm_tree *tr, const tm_count_args *args, con
         prm.poll_every = P.poll_every;
         prm.donate_seq = P.donate_seq;
         prm.donate_leaf = P.donate_leaf;
-        prm.pad2 = 0;
+        prm.siblings = P.siblings ? 1 : 0;
+        prm.sib_always = args->sibling_always ? 1 : 0;
+        prm.offload_max = args->offload_max > 0 ? args->offload_max : kOffloadMax;
         prm.root_qmask = P.root_qmask;
         const SpecKernel *sk = (P.spec && !P.root_qmask) ? spec_kernel(tr, P.comine ? 0 : 1 + L) : nullptr;
         cudaError_t e;
@@ -507,7 +511,7 @@ extern "C" int tm_autotune(const tm_graph *g, const tm_tree *tr, const tm_count_
     const int polls[] = {1, 4, 16};
     for (int pass = 0; pass < 2; pass++) {
         for (int c : ctas) { tm_tune t = cur; t.ctas_per_sm = c; float ms; TM_TRY(timed(apply(t), &ms)); if (ms < cur_ms) { cur = t; cur_ms = ms; } }
-        if (!(a.mode & TM_SCHED_DYNAMIC)) break;
+        if (!(a.mode & (TM_SCHED_DYNAMIC | TM_SCHED_SIBLINGS))) break;
         for (int v : seqs) { tm_tune t = cur; t.donate_seq = v; float ms; TM_TRY(timed(apply(t), &ms)); if (ms < cur_ms) { cur = t; cur_ms = ms; } }
         for (int v : leaves) { tm_tune t = cur; t.donate_leaf = v; float ms; TM_TRY(timed(apply(t), &ms)); if (ms < cur_ms) { cur = t; cur_ms = ms; } }
         for (int v : polls) { tm_tune t = cur; t.poll_every = v; float ms; TM_TRY(timed(apply(t), &ms)); if (ms < cur_ms) { cur = t; cur_ms = ms; } }
@@ -636,7 +640,9 @@ extern "C" int tm_count_noalloc(const tm_graph *g, const tm_tree *tr, const int3
         prm.poll_every = kPollEvery;
         prm.donate_seq = kDonateSeq;
         prm.donate_leaf = kDonateLeaf;
-        prm.pad2 = 0;
+        prm.siblings = 0;
+        prm.sib_always = 0;
+        prm.offload_max = kOffloadMax;
         prm.root_qmask = nullptr;
         k_mine<false><<<blocks, kThreads, dyn_smem, s>>>(prm);
         TM_CUDA_TRY(cudaGetLastError());

@@ -38,6 +38,7 @@ TM_LEAF_SCAN = 0x10
 TM_SCHED_DYNAMIC = 0x100
 TM_SCHED_PLANNED = 0x200
 TM_GENERIC = 0x1000
+TM_SCHED_SIBLINGS = 0x400
 TM_COMPILE_CHAINS = 0x1
 TM_COMPILE_CHECK = 0x2
 TM_SPEC_MAX_NODES = 256
@@ -86,9 +87,9 @@ class tm_count_args(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_uint32), ("flags", ctypes.c_uint32), ("roots", ctypes.c_void_p),
                 ("n_roots", ctypes.c_int64), ("root_lo", ctypes.c_int64), ("root_hi", ctypes.c_int64),
                 ("per_root_counts", ctypes.c_void_p), ("per_root_work", ctypes.c_void_p),
-                ("ctas_per_sm", ctypes.c_int32), ("reserved", ctypes.c_int32), ("root_split", ctypes.c_void_p),
+                ("ctas_per_sm", ctypes.c_int32), ("offload_max", ctypes.c_int32), ("root_split", ctypes.c_void_p),
                 ("poll_every", ctypes.c_int32), ("donate_seq", ctypes.c_int32), ("donate_leaf", ctypes.c_int32),
-                ("reserved2", ctypes.c_int32)]
+                ("sibling_always", ctypes.c_int32)]
 
 
 class tm_server_config(ctypes.Structure):
@@ -360,6 +361,8 @@ def _count_args(mode=TM_COMINE, roots=None, root_lo=0, root_hi=0, per_root_count
         a.donate_seq = tune["donate_seq"]
         a.donate_leaf = tune["donate_leaf"]
         a.poll_every = tune["poll_every"]
+        a.offload_max = tune.get("offload_max", 0)
+        a.sibling_always = tune.get("sibling_always", 0)
     return a, keep
 
 
