@@ -618,6 +618,10 @@ def main():
     ap.add_argument("--no-permotif", action="store_true")
     ap.add_argument("--static", action="store_true", help="one warp per root, no subtree splitting")
     ap.add_argument("--generic", action="store_true", help="the table-driven kernel only (no code generation)")
+    ap.add_argument("--with-static", action="store_true",
+                    help="also time the step with static scheduling (one warp per root; slow on hub roots)")
+    ap.add_argument("--thread-work", type=float, default=100.0,
+                    help="thread tier: roots predicted below this work run one per lane (0: no tier)")
     ap.add_argument("--no-learned", action="store_true")
     ap.add_argument("--train-roots", type=int, default=512)
     ap.add_argument("--unit-work", type=float, default=1e6)
@@ -687,29 +691,31 @@ def main():
     ro = torch.zeros_like(d_roots)
     sp = torch.zeros_like(d_roots)
 
-    def plan(gh, th, r_dev, f, r_out, s_out):
+    def plan(gh, th, r_dev, f, r_out, s_out, thread_work=0.0):
         tmotif.tm_features(gh, th, r_dev, f, stream=stream)
-        model.plan(f, r_dev, r_out, s_out, unit_work=args.unit_work, max_split=args.max_split, stream=stream)
+        model.plan(f, r_dev, r_out, s_out, unit_work=args.unit_work, max_split=args.max_split, stream=stream,
+                   thread_work=thread_work)
 
     # reactive-splitting tunables (chunk loads between looks for idle warps, the
     # shortest counting-only slice worth handing over), from a sweep on this workload
     tune = {"ctas_per_sm": 0, "donate_seq": 0, "donate_leaf": args.donate_leaf, "poll_every": args.poll_every}
 
-    def step(m, use_model):
+    def step(m, use_model, thread_work=0.0):
         if use_model:
-            plan(g.h, tr.h, d_roots, feats, ro, sp)
-            tmotif.tm_count(g.h, tr.h, mode=m | tmotif.TM_SCHED_PLANNED, roots=ro, counts=counts, root_split=sp,
-                            stream=stream, tune=tune)
+            plan(g.h, tr.h, d_roots, feats, ro, sp, thread_work)
+            tiers = tmotif.TM_SCHED_TIERS if thread_work > 0 else 0
+            tmotif.tm_count(g.h, tr.h, mode=m | tmotif.TM_SCHED_PLANNED | tiers, roots=ro, counts=counts,
+                            root_split=sp, stream=stream, tune=tune)
         else:
             tmotif.tm_count(g.h, tr.h, mode=m, roots=d_roots, counts=counts, stream=stream, tune=tune)
 
-    def timed(m, use_model, n):
+    def timed(m, use_model, n, thread_work=0.0):
         ts = []
         for i in range(n):
             flush.fill_(i & 0xFF)
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record(stream)
-            step(m, use_model)
+            step(m, use_model, thread_work)
             b.record(stream)
             torch.cuda.synchronize()
             ts.append(a.elapsed_time(b))
@@ -763,6 +769,17 @@ def main():
     # the same step with the paper's sibling splitting and multi-offload in
     # place of halving slices for idle warps
     siblings = timed(mode | tmotif.TM_SCHED_SIBLINGS, use_model, n_cmp) if not args.static else None
+    # the same step with a thread tier: roots predicted below --thread-work one per lane
+    tiers = tier_hist = None
+    if use_model and args.thread_work > 0:
+        tiers = timed(mode, True, n_cmp, args.thread_work)
+        plan(g.h, tr.h, d_roots, feats, ro, sp, args.thread_work)
+        _, st_t = tmotif.tm_count(g.h, tr.h, mode=mode | tmotif.TM_SCHED_PLANNED | tmotif.TM_SCHED_TIERS, roots=ro,
+                                  root_split=sp, stats=True, stream=stream, tune=tune)
+        tier_hist = {"thread": st_t["roots_thread_tier"], "split": st_t["roots_split"],
+                     "warp": st_t["n_roots"] - st_t["roots_thread_tier"] - st_t["roots_split"]}
+    # the same step, static: one warp per root, no plan, no queue
+    static = timed(mode & ~tmotif.TM_SCHED_DYNAMIC, False, n_cmp) if args.with_static and not args.static else None
 
     # per-motif comparator on the same roots (one chain tree per motif), same schedule
     perm = perm_reactive = None
@@ -832,6 +849,8 @@ def main():
         "generic_ms_per_step": generic,
         "specialised_speedup_vs_generic": (generic / ms_step) if generic else None,
         "siblings_ms_per_step": siblings,
+        "tiers_ms_per_step": tiers, "thread_work": args.thread_work, "tier_histogram": tier_hist,
+        "static_ms_per_step": static,
         "schedule_siblings": "the same step with sibling splitting and multi-offload (TM_SCHED_SIBLINGS)",
         "permotif_ms_per_step": perm,
         "comine_speedup_vs_permotif": (perm / ms_step) if perm else None,

@@ -184,6 +184,11 @@ int tm_tree_compile(tm_tree *tr, uint32_t flags, tm_compile_info *info);
 #define TM_SCHED_DYNAMIC 0x100u /* persistent launch, heavy subtrees split across warps */
 #define TM_SCHED_PLANNED 0x200u /* persistent launch; cut root i's first-level lists into root_split[i] slices */
 #define TM_GENERIC 0x1000u    /* the table-driven kernel even when the tree has a specialised one */
+#define TM_SCHED_TIERS 0x800u /* with TM_SCHED_PLANNED: the roots at the tail of the order whose
+                                 root_split is 0 (tm_plan_tiers marks those predicted light) run one
+                                 per lane (thread tier); the others one per warp (warp tier), those
+                                 with root_split > 1 cut into slices for many warps.  Ignored for
+                                 trees of more than 8 windows */
 #define TM_SCHED_SIBLINGS 0x400u /* TM_SCHED_DYNAMIC with the paper's sibling splitting (a warp about to
                                     descend into several children hands all but the first to idle
                                     warps as separate tasks) and multi-offload (a donation hands
@@ -237,6 +242,9 @@ typedef struct {
     int64_t idle_expired;     /* warps of the persistent launch whose bounded idle wait ran out
                                  while other warps still held work (they left the launch early;
                                  counts are unaffected) */
+    int64_t roots_thread_tier; /* tier histogram: roots counted one per lane (TM_SCHED_TIERS) */
+    int64_t roots_split;      /* ... roots whose first-level lists were cut into planned slices;
+                                 the rest (n_roots - both) ran one per warp */
 } tm_run_stats;
 
 /*
@@ -493,6 +501,11 @@ int tm_model_train(tm_model *m, const float *feats, const float *labels, int64_t
  * unit_work of predicted work.  Pass both to tm_count with TM_SCHED_PLANNED. */
 int tm_plan(const tm_model *m, const float *feats, const int32_t *roots, int64_t n, double unit_work,
             int32_t max_split, int32_t *roots_out, int32_t *split_out, void *stream);
+/* The same with tiers: roots whose predicted work is below thread_work get
+ * split_out 0, which TM_SCHED_TIERS runs one per lane; being the least
+ * predicted, they form the tail of roots_out. */
+int tm_plan_tiers(const tm_model *m, const float *feats, const int32_t *roots, int64_t n, double unit_work,
+                  int32_t max_split, double thread_work, int32_t *roots_out, int32_t *split_out, void *stream);
 
 /* Message describing the last error on the calling thread ("" if none). */
 const char *tm_last_error(void);

@@ -126,7 +126,7 @@ int tm_count(const tm_graph *g, const tm_tree *tr, const tm_count_args *args, in
     g_last_error.clear();
     if (!g || !tr || !args || !counts) { set_error("tm_count: NULL argument"); return TM_EINVAL; }
     if (args->mode & ~(TM_PERMOTIF | TM_AUTO | TM_LEAF_SCAN | TM_SCHED_DYNAMIC | TM_SCHED_PLANNED | TM_SCHED_SIBLINGS |
-                       TM_GENERIC)) {
+                       TM_SCHED_TIERS | TM_GENERIC)) {
         set_error("tm_count: unknown mode bit");
         return TM_EINVAL;
     }

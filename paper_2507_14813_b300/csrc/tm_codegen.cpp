@@ -186,7 +186,7 @@ int compile(const std::string &src, SpecKernel *k, bool load) {
         set_error("tm_tree_compile: nvrtcCreateProgram failed");
         return TM_ECUDA;
     }
-    const char *expr = "tmo::dev::k_mine<false>";   // the counting launch; stats launches stay table-driven
+    const char *expr = "tmo::dev::k_mine<false, false>";   // counting launches without a thread tier
     nvrtcAddNameExpression(prog, expr);
     // a compile-only check also asks the assembler for its register and spill report
     const char *opts[] = {"--gpu-architecture=sm_103a", "-std=c++17", "-lineinfo", "-DNDEBUG",

@@ -94,6 +94,7 @@ constexpr int kThreads = kWarps * 32;
 constexpr int kSmemCounters = 2048;       // per-CTA counters kept in shared memory up to this many
 constexpr int kWarpCounters = kSmemCounters / kWarps;  // up to this many: one private slice per warp
 constexpr int kLaneScanMax = 24;          // leaf windows up to this size are scanned by the lane
+constexpr int kLaneDeltas = 8;            // thread tier: trees with at most this many windows
 constexpr uint32_t kCacheEmpty = 0xffffffffu;
 constexpr unsigned long long kSlotEmpty = (unsigned long long)kCacheEmpty << 32;
 constexpr int kSlots = 256;               // occurrence-table slots per warp
@@ -138,6 +139,8 @@ enum : int { kErrTimeout = 1,          // a bounded wait expired
 
 struct QueueHdr {
     unsigned long long root_cursor;
+    unsigned long long lane_cursor;   // thread tier: roots handed out, 32 per warp
+    long long lane_from;              // thread tier: first root index (the tail of a planned order)
     unsigned int head;        // next task to claim
     unsigned int tail;        // tasks reserved by donors
     int idle;                 // warps waiting for work
@@ -170,13 +173,16 @@ struct Params {
     int32_t siblings;                 // 1: sibling splitting and multi-offload (TM_SCHED_SIBLINGS)
     int32_t sib_always;               // 1: split siblings even when no warp is idle
     int32_t offload_max;              // most pieces one donation hands over (multi-offload)
+    int32_t tiers;                    // 1: roots from q->lane_from on run one per lane (thread tier)
     const uint64_t *root_qmask;       // per root index: queries it serves (bit q), or null = all
 };
 
 // kStLogDeg: sum over opened lists of ceil(log2(list length + 1)), the
 // probes a binary search of each list costs
+// kStLaneRoots: roots counted by the thread tier; kStSplitRoots: roots whose
+// first-level lists were cut into planned slices
 enum { kStCand = 0, kStExp, kStListProbe, kStHashProbe, kStPairProbe, kStLeaf, kStRoots, kStSplit, kStLogDeg,
-       kStatFields };
+       kStLaneRoots, kStSplitRoots, kStatFields };
 // after the kStatFields totals: busy cycles of the busiest warp, their sum, and the warps
 enum { kBusyMax = 0, kBusySum, kBusyWarps, kBusyFields };
 
@@ -392,7 +398,9 @@ __device__ __forceinline__ int64_t run_tail(const int32_t *__restrict__ a, int64
     return lo - p;
 }
 
-template <bool kStats>
+// kExt: the extended schedules (thread tier, sibling splitting, multi-offload)
+// are compiled in; the default kernel leaves them out.
+template <bool kStats, bool kExt>
 struct Miner {
     const Params &p;
     WarpState &ws;
@@ -449,23 +457,28 @@ struct Miner {
     // last) at level lv - 1.
     __device__ int64_t leaf_count(const DevNode &L, int lv, int uk, int vk, int32_t cs, int32_t cd, int32_t last,
                                   int32_t hi) {
+        const int nv = L.nvb[lv];                       // labels mapped before the leaf edge
+        int32_t img[kMaxV];
+#pragma unroll
+        for (int l = 0; l < kMaxV; l++) img[l] = (l < nv) ? lab(l, uk, vk, cs, cd) : -1;
+        return leaf_count_img(L, lv, img, cs, cd, last, hi);
+    }
+
+    // The same for a full mapping img[0 .. L.nvb[lv]) of the motif labels
+    // (cs -> cd: the endpoints of edge `last`).
+    __device__ int64_t leaf_count_img(const DevNode &L, int lv, const int32_t *img, int32_t cs, int32_t cd,
+                                      int32_t last, int32_t hi) {
         const DevGraph &g = p.g;
         const int u = L.eu[lv], v = L.ev[lv];
         const int nv = L.nvb[lv];                       // labels mapped before the leaf edge
         const bool um = u < nv, vm = v < nv;
-        int32_t img[kMaxV];
-#pragma unroll
-        for (int l = 0; l < kMaxV; l++) img[l] = (l < nv) ? lab(l, uk, vk, cs, cd) : -1;
         unsigned long long hp = 0, pp = 0, lp = 0, sc = 0;
         int64_t c = 0;
         if (um && vm) {
-            int32_t xu = u == uk ? cs : (u == vk ? cd : ws.m2g[u]);
-            int32_t xv = v == uk ? cs : (v == vk ? cd : ws.m2g[v]);
-            c = pair_count(g, xu, xv, last, hi, hp, pp);
+            c = pair_count(g, img[u], img[v], last, hi, hp, pp);
         } else {
             const bool out = um;
-            const int32_t x = out ? (u == uk ? cs : (u == vk ? cd : ws.m2g[u]))
-                                  : (v == uk ? cs : (v == vk ? cd : ws.m2g[v]));
+            const int32_t x = out ? img[u] : img[v];
             const int2 *adj = out ? g.out_adj : g.in_adj;
             const int64_t *off = out ? g.out_off : g.in_off;
             int64_t b0 = __ldg(off + x), b1 = __ldg(off + x + 1);
@@ -914,7 +927,7 @@ struct Miner {
             const int64_t pos = ws.pos[kb], end = ws.end[kb];
             const int64_t rem = end - pos;
             if (rem < (ws.seq[kb] ? p.donate_seq : p.donate_leaf)) continue;
-            if (p.siblings) {                          // multi-offload
+            if (kExt && p.siblings) {                  // multi-offload
                 offload(kb, idle);
                 return;
             }
@@ -1314,7 +1327,7 @@ struct Miner {
                 if (k == N.k_end - 1) {
                     if (N.n_seq > 0 && chk(k + 1 < kMaxE)) {
                         int sib_end = N.child_begin + N.n_seq;
-                        if (p.siblings && N.n_seq > 1) sib_end = split_siblings(k + 1, N.child_begin, sib_end);
+                        if (kExt && p.siblings && N.n_seq > 1) sib_end = split_siblings(k + 1, N.child_begin, sib_end);
                         open(k + 1, N.child_begin, sib_end);
                         k++;
                     }
@@ -1366,6 +1379,176 @@ struct Miner {
         run(0);
     }
 
+    // ---------------------------------------------------------------- thread tier
+
+    // Counts of one lane's root go to the shared counters with atomics (the
+    // lanes of the warp add at once).
+    __device__ __forceinline__ void add_count_lane(int32_t counter, unsigned long long c) {
+        if (c == 0) return;
+        if (!chk(counter >= 0 && counter < TM_NCOUNTERS)) return;
+        if (p.smem_counters) atomicAdd(&s_cnt[counter], c);
+        else atomicAdd(&p.counts[counter], c);
+        if (p.per_root_counts)
+            atomicAdd((unsigned long long *)&p.per_root_counts[ri * TM_NCOUNTERS + counter], c);
+    }
+
+    // The lane's frames of its own walk: per level, the node, its siblings'
+    // end, the list kind and the unscanned positions [pos, end).
+    struct LaneFrames {
+        int16_t node[kMaxE], sib[kMaxE];
+        int8_t lt[kMaxE];
+        int32_t pos[kMaxE], end[kMaxE];
+        int32_t eid[kMaxE];
+        int32_t m2g[kMaxV];
+        int32_t eh[kLaneDeltas];
+    };
+
+    // Open level k of `node` (siblings up to sib) on the lane's own frames:
+    // the slice of its candidate list with edge ids in (eid[k-1], window end].
+    __device__ void lane_open(LaneFrames &F, int k, int node, int sib) {
+        const DevNode &N = TM_NODE(node);
+        F.node[k] = (int16_t)node;
+        F.sib[k] = (int16_t)sib;
+        F.pos[k] = 0;
+        F.end[k] = 0;
+        F.lt[k] = kListGlobal;
+        if (!(N.qmask & rmask)) return;
+        const int32_t last = F.eid[k - 1];
+        const int32_t hi = F.eh[N.dmax];
+        const int u = N.eu[k], v = N.ev[k], nv = N.nvb[k];
+        const bool um = u < nv, vm = v < nv;
+        int8_t lt = kListGlobal;
+        int32_t x = 0;
+        if (um && vm) {
+            const int32_t xu = F.m2g[u], xv = F.m2g[v];
+            const int64_t du = __ldg(p.g.out_off + xu + 1) - __ldg(p.g.out_off + xu);
+            const int64_t dv = __ldg(p.g.in_off + xv + 1) - __ldg(p.g.in_off + xv);
+            if (du <= dv) { lt = kListOut; x = xu; } else { lt = kListIn; x = xv; }
+        } else if (um) { lt = kListOut; x = F.m2g[u]; }
+        else if (vm) { lt = kListIn; x = F.m2g[v]; }
+        F.lt[k] = lt;
+        if (lt == kListGlobal) {
+            F.pos[k] = last + 1;
+            F.end[k] = hi + 1;
+            return;
+        }
+        const bool out = lt == kListOut;
+        const int64_t *off = out ? p.g.out_off : p.g.in_off;
+        const int2 *adj = out ? p.g.out_adj : p.g.in_adj;
+        const int64_t b0 = __ldg(off + x), b1 = __ldg(off + x + 1);
+        unsigned long long lp = 0;
+        int64_t a = after_pos(p.g, out, x, last, F.m2g[N.eu[k - 1]], F.m2g[N.ev[k - 1]]);
+        if (a < 0) a = lane_upper(adj, b0, b1, last, lp);
+        const int64_t b = lane_gallop(adj, a, b1, hi, lp);
+        F.pos[k] = (int32_t)a;
+        F.end[k] = (int32_t)b;
+        if (kStats) {
+            w.v[kStListProbe] += lp;
+            w.v[kStExp]++;
+            w.v[kStLogDeg] += (unsigned long long)(64 - __clzll((unsigned long long)(b1 - b0)));
+        }
+    }
+
+    // Level k of `node` has just been matched (F.eid[k], F.m2g): count what
+    // completes here and open the next level; returns the deepest open level.
+    __device__ int lane_matched(LaneFrames &F, int k, int node) {
+        const DevNode &N = TM_NODE(node);
+        const int32_t last = F.eid[k];
+        const int32_t cs = F.m2g[N.eu[k]], cd = F.m2g[N.ev[k]];
+        if (k == N.k_end - 1) {                         // C_N complete: Q_N, then the children
+            for (int i = 0; i < N.n_ref; i++) {
+                const DevRef ref = TM_REF(N.ref_begin + i);
+                if (((rmask >> ref.query) & 1ull) && last <= F.eh[ref.delta]) add_count_lane(ref.counter, 1);
+            }
+            for (int ci = 0; ci < N.n_par; ci++) {
+                const DevNode &L = TM_NODE(N.child_begin + N.n_seq + ci);
+                for (int i = 0; i < L.n_ref; i++) {
+                    const DevRef ref = TM_REF(L.ref_begin + i);
+                    const int32_t hi = F.eh[ref.delta];
+                    if (((rmask >> ref.query) & 1ull) && last < hi)
+                        add_count_lane(ref.counter, (unsigned long long)leaf_count_img(L, k + 1, F.m2g, cs, cd, last, hi));
+                }
+            }
+            if (N.n_seq > 0 && chk(k + 1 < kMaxE)) {
+                lane_open(F, k + 1, N.child_begin, N.child_begin + N.n_seq);
+                return k + 1;
+            }
+            return k;
+        }
+        if ((N.flags & kNodeParLeaf) && k == N.k_end - 2) {   // N's last edge counted from here
+            for (int i = 0; i < N.n_ref; i++) {
+                const DevRef ref = TM_REF(N.ref_begin + i);
+                const int32_t hi = F.eh[ref.delta];
+                if (((rmask >> ref.query) & 1ull) && last < hi)
+                    add_count_lane(ref.counter, (unsigned long long)leaf_count_img(N, k + 1, F.m2g, cs, cd, last, hi));
+            }
+            return k;
+        }
+        if (!chk(k + 1 < kMaxE)) return k;
+        lane_open(F, k + 1, node, node + 1);
+        return k + 1;
+    }
+
+    // Root edge r on this lane alone: Algorithm 3 as a serial depth-first
+    // walk over the lane's own frames (no warp collectives), the single-edge
+    // leaves counted by the same window arithmetic as the warp tier.
+    __device__ void lane_root(int32_t r) {
+        const DevGraph &g = p.g;
+        const int32_t a = __ldg(g.src + r), b = __ldg(g.dst + r);
+        if (a == b) return;                             // injective map needs a != b
+        LaneFrames F;
+        const int64_t t0 = __ldg(g.t + r);
+#pragma unroll
+        for (int d = 0; d < kLaneDeltas; d++) {
+            F.eh[d] = -1;
+            if (d < TM_NDELTAS) {
+                unsigned long long pr = 0;
+                F.eh[d] = window_end(g.t, g.E, r, sat_add(t0, TM_DELTA(d)), pr);
+                if (kStats) w.v[kStListProbe] += pr;
+            }
+        }
+#pragma unroll
+        for (int l = 0; l < kMaxV; l++) F.m2g[l] = -1;
+        F.m2g[0] = a;                                   // the root edge is canonical 0 -> 1
+        F.m2g[1] = b;
+        F.eid[0] = r;
+        int k = lane_matched(F, 0, 0);
+        while (k >= 1) {
+            if (F.pos[k] < F.end[k]) {
+                const int32_t i = F.pos[k]++;
+                const DevNode &N = TM_NODE(F.node[k]);
+                const int u = N.eu[k], v = N.ev[k], nv = N.nvb[k];
+                int32_t e, s, d;
+                if (F.lt[k] == kListOut) {
+                    const int2 c = __ldg(p.g.out_adj + i);
+                    e = c.y; s = F.m2g[u]; d = c.x;
+                } else if (F.lt[k] == kListIn) {
+                    const int2 c = __ldg(p.g.in_adj + i);
+                    e = c.y; s = c.x; d = F.m2g[v];
+                } else {
+                    e = i; s = __ldg(g.src + i); d = __ldg(g.dst + i);
+                }
+                if (kStats) w.v[kStCand]++;
+                // structure with full injectivity (reading 3)
+                bool ok = (u >= nv || s == F.m2g[u]) && (v >= nv || d == F.m2g[v]) && (u < nv || v < nv || s != d);
+#pragma unroll
+                for (int l = 0; l < kMaxV; l++)
+                    if (l < nv) ok &= (u < nv || s != F.m2g[l]) && (v < nv || d != F.m2g[l]);
+                if (!ok) continue;
+                F.eid[k] = e;
+                F.m2g[u] = s;
+                F.m2g[v] = d;
+                k = lane_matched(F, k, F.node[k]);
+                continue;
+            }
+            if (F.node[k] + 1 < F.sib[k]) {                 // next sibling from the same partial match
+                lane_open(F, k, F.node[k] + 1, F.sib[k]);
+                continue;
+            }
+            k--;
+        }
+    }
+
     // A donated slice: rebuild the partial match, then walk its subtree.
     __device__ void task(const Task &tk) {
         const DevGraph &g = p.g;
@@ -1384,7 +1567,7 @@ struct Miner {
             }
         }
         __syncwarp();
-        if (tk.lo < 0) {                               // a sibling task: this node's subtree alone
+        if (kExt && tk.lo < 0) {                       // a sibling task: this node's subtree alone
             if (lane == 0) ws.cache_owner = -1;
             __syncwarp();
             open(k, tk.node, tk.node + 1);
@@ -1407,8 +1590,8 @@ struct Miner {
     }
 };
 
-template <bool kStats>
-__device__ void flush_work(Miner<kStats> &M, const Work &before, const Params &p, int lane) {
+template <bool kStats, bool kExt>
+__device__ void flush_work(Miner<kStats, kExt> &M, const Work &before, const Params &p, int lane) {
     if (!kStats || !p.per_root_work) return;
     unsigned long long d[4];
     d[0] = warp_sum_u64(M.w.v[kStCand] - before.v[kStCand]);
@@ -1421,7 +1604,10 @@ __device__ void flush_work(Miner<kStats> &M, const Work &before, const Params &p
             if (d[f]) atomicAdd((unsigned long long *)&p.per_root_work[M.ri * TM_WORK_FIELDS + f], d[f]);
 }
 
-template <bool kStats>
+// kExt: the launch may use the extended schedules (a thread tier,
+// TM_SCHED_TIERS; sibling splitting and multi-offload, TM_SCHED_SIBLINGS);
+// only such launches carry their code.
+template <bool kStats, bool kExt>
 #ifndef TM_MIN_BLOCKS
 #define TM_MIN_BLOCKS 3   // CTAs per SM the register budget is sized for (80 registers per thread)
 #endif
@@ -1433,7 +1619,7 @@ __global__ void __launch_bounds__(kThreads, TM_MIN_BLOCKS) k_mine(Params p) {
     const int n_smem = p.smem_counters == 2 ? kWarps * n_cnt : (p.smem_counters ? n_cnt : 0);
     for (int i = threadIdx.x; i < n_smem; i += blockDim.x) s_cnt[i] = 0;
     __syncthreads();
-    Miner<kStats> M(p, s_ws[warp], s_cnt + (p.smem_counters == 2 ? warp * n_cnt : 0), lane);
+    Miner<kStats, kExt> M(p, s_ws[warp], s_cnt + (p.smem_counters == 2 ? warp * n_cnt : 0), lane);
     if (p.dynamic && lane == 0) atomicAdd(&p.q->busy, 1);
     // stats launch: this warp's cycles spent other than waiting for work
     const long long t_begin = kStats ? clock64() : 0;
@@ -1454,11 +1640,13 @@ __global__ void __launch_bounds__(kThreads, TM_MIN_BLOCKS) k_mine(Params p) {
                 continue;
             }
         }
+        // warp tier: roots [0, n_warp); the thread tier takes the rest
+        const int64_t n_warp = (kExt && p.tiers) ? min((int64_t)p.q->lane_from, p.n_roots) : p.n_roots;
         unsigned long long first = 0;
         if (lane == 0) first = atomicAdd(&p.q->root_cursor, (unsigned long long)p.chunk);
         first = __shfl_sync(0xffffffffu, first, 0);
-        if (first < (unsigned long long)p.n_roots) {
-            const int64_t last = min((int64_t)first + p.chunk, p.n_roots);
+        if (first < (unsigned long long)n_warp) {
+            const int64_t last = min((int64_t)first + p.chunk, n_warp);
             for (int64_t ri = (int64_t)first; ri < last; ri++) {
                 M.ri = ri;
                 M.split_h = p.split ? __ldg(p.split + ri) : 0;
@@ -1469,11 +1657,47 @@ __global__ void __launch_bounds__(kThreads, TM_MIN_BLOCKS) k_mine(Params p) {
                     continue;
                 }
                 Work before = M.w;
+                if (kStats && lane == 0 && M.split_h > 1) M.w.v[kStSplitRoots]++;
                 M.root(r);
                 if (kStats && lane == 0) M.w.v[kStRoots]++;
                 flush_work(M, before, p, lane);
             }
             continue;
+        }
+        if (kExt && p.tiers) {                           // thread tier: 32 roots, one per lane
+            unsigned long long b = 0;
+            if (lane == 0) b = atomicAdd(&p.q->lane_cursor, 32ull);
+            b = __shfl_sync(0xffffffffu, b, 0);
+            const int64_t base = n_warp + (int64_t)b;
+            if (base < p.n_roots) {
+                const int64_t ri = base + lane;
+                if (ri < p.n_roots) {
+                    const int32_t r = p.roots ? __ldg(p.roots + ri) : (int32_t)(p.root_lo + ri);
+                    if (r < 0 || r >= p.g.E) {
+                        atomicOr(&p.q->error, kErrBadRoot);
+                    } else {
+                        M.ri = ri;
+                        M.rmask = p.root_qmask ? __ldg(p.root_qmask + ri) : ~0ull;
+                        Work before = M.w;
+                        M.lane_root(r);
+                        if (kStats) {
+                            M.w.v[kStRoots]++;
+                            M.w.v[kStLaneRoots]++;
+                            if (p.per_root_work) {              // this lane's root alone
+                                unsigned long long d[4] = {
+                                    M.w.v[kStCand] - before.v[kStCand], M.w.v[kStExp] - before.v[kStExp],
+                                    M.w.v[kStListProbe] + M.w.v[kStHashProbe] + M.w.v[kStPairProbe] -
+                                        before.v[kStListProbe] - before.v[kStHashProbe] - before.v[kStPairProbe],
+                                    M.w.v[kStLeaf] - before.v[kStLeaf]};
+                                for (int f = 0; f < 4; f++)
+                                    if (d[f]) atomicAdd((unsigned long long *)&p.per_root_work[ri * TM_WORK_FIELDS + f], d[f]);
+                            }
+                        }
+                    }
+                }
+                __syncwarp();
+                continue;
+            }
         }
         if (!p.dynamic) break;
         const long long tw = kStats ? clock64() : 0;
@@ -1501,6 +1725,19 @@ __global__ void __launch_bounds__(kThreads, TM_MIN_BLOCKS) k_mine(Params p) {
                 for (int wi = 1; wi < kWarps; wi++) c += s_cnt[wi * n_cnt + i];
             if (c) atomicAdd(&p.counts[i], c);
         }
+}
+
+// The thread tier's first root: the tail of a planned order whose slice
+// count is 0 (the plan marks roots predicted light so; counts are
+// non-increasing along the order, found by binary search).
+__global__ void k_tier_bound(const int32_t *split, int64_t n, QueueHdr *q) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    int64_t lo = 0, hi = n;
+    while (lo < hi) {
+        const int64_t mid = lo + (hi - lo) / 2;
+        if (split[mid] > 0) lo = mid + 1; else hi = mid;
+    }
+    q->lane_from = lo;
 }
 
 __global__ void k_to_i64(const unsigned long long *a, int64_t *b, int n) {

@@ -30,8 +30,10 @@ int allow_counter_smem() {
     TM_CUDA_TRY(cudaGetDevice(&dev));
     if (dev >= 0 && dev < 64 && done[dev]) return TM_OK;
     const int bytes = (int)(sizeof(unsigned long long) * kSmemCounters);
-    TM_CUDA_TRY(cudaFuncSetAttribute(k_mine<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
-    TM_CUDA_TRY(cudaFuncSetAttribute(k_mine<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+    TM_CUDA_TRY(cudaFuncSetAttribute(k_mine<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+    TM_CUDA_TRY(cudaFuncSetAttribute(k_mine<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+    TM_CUDA_TRY(cudaFuncSetAttribute(k_mine<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+    TM_CUDA_TRY(cudaFuncSetAttribute(k_mine<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
     if (dev >= 0 && dev < 64) done[dev] = 1;
     return TM_OK;
 }
@@ -43,6 +45,7 @@ struct Plan {
     bool comine = true, par = true, react = false, planned = false, dynamic = false, stats = false;
     bool spec = false;                  // counting launches may use the tree's specialised kernels
     bool siblings = false;              // sibling splitting and multi-offload
+    bool tiers = false;                 // the planned order's light tail runs one root per lane
     int64_t n_roots = 0, root_lo = 0;
     const int32_t *roots = nullptr;     // device
     const uint64_t *root_qmask = nullptr; // device, serving batches only
@@ -52,6 +55,13 @@ struct Plan {
     int poll_every = kPollEvery, donate_seq = kDonateSeq, donate_leaf = kDonateLeaf;
     size_t o_q = 0, o_tasks = 0, o_ready = 0, bytes = 0, b_ready = 0;
 };
+
+// The table-driven kernel for a launch: stats or not, thread tier or not.
+using MineKernel = void (*)(Params);
+MineKernel kernel_of(bool stats, bool ext) {
+    if (ext) return stats ? k_mine<true, true> : k_mine<false, true>;
+    return stats ? k_mine<true, false> : k_mine<false, false>;
+}
 
 // roots a warp claims at a time: 1, or up to 16 when there are many roots per warp
 int32_t chunk_for(int64_t n_roots, int blocks) {
@@ -64,11 +74,14 @@ int make_plan(const tm_graph *g, const tm_tree *tr, const tm_count_args *args, b
     P->comine = (args->mode & TM_PERMOTIF) == 0;
     P->par = (args->mode & TM_LEAF_SCAN) == 0;
     P->siblings = (args->mode & TM_SCHED_SIBLINGS) != 0;
+    // the thread tier keeps a window end per window in each lane: at most kLaneDeltas
+    P->tiers = (args->mode & TM_SCHED_TIERS) && (args->mode & TM_SCHED_PLANNED) && tr->h.n_deltas <= kLaneDeltas;
     P->react = (args->mode & (TM_SCHED_DYNAMIC | TM_SCHED_SIBLINGS)) != 0;
     P->planned = (args->mode & TM_SCHED_PLANNED) != 0;
     P->dynamic = P->react || P->planned;
     P->stats = stats;
-    P->spec = !(args->mode & TM_GENERIC) && P->par && !stats;
+    // the runtime-compiled kernels are the default schedules' (no extended ones)
+    P->spec = !(args->mode & TM_GENERIC) && P->par && !stats && !(args->mode & (TM_SCHED_TIERS | TM_SCHED_SIBLINGS));
     if (P->planned && !args->root_split) {
         set_error("tm_count: TM_SCHED_PLANNED needs root_split");
         return TM_EINVAL;
@@ -107,7 +120,7 @@ int make_plan(const tm_graph *g, const tm_tree *tr, const tm_count_args *args, b
     P->dyn_smem = (int)(sizeof(unsigned long long) * P->n_motifs) * (P->warp_cnt ? kWarps : P->smem_cnt ? 1 : 0);
     TM_TRY(allow_counter_smem());
     int per_sm = 0;
-    TM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, stats ? k_mine<true> : k_mine<false>,
+    TM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel_of(stats, P->tiers || P->siblings),
                                                               kThreads, P->dyn_smem));
     P->ctas_cap = args->ctas_per_sm;
     P->n_sm = n_sm;
@@ -150,7 +163,7 @@ int enqueue(const tm_graph *g, const tm_tree *tr, const tm_count_args *args, con
         TM_CUDA_TRY(cudaMemsetAsync(args->per_root_counts, 0, sizeof(int64_t) * P.n_roots * P.n_motifs, s));
     if (args->per_root_work && P.n_roots > 0)
         TM_CUDA_TRY(cudaMemsetAsync(args->per_root_work, 0, sizeof(int64_t) * P.n_roots * TM_WORK_FIELDS, s));
-    auto kern = P.stats ? k_mine<true> : k_mine<false>;
+    auto kern = kernel_of(P.stats, P.tiers || P.siblings);
     int64_t n = 0;
     for (int L = 0; L < P.n_launch && P.n_roots > 0; L++) {
         DevTree dt;
@@ -181,7 +194,12 @@ int enqueue(const tm_graph *g, const tm_tree *tr, const tm_count_args *args, con
         prm.siblings = P.siblings ? 1 : 0;
         prm.sib_always = args->sibling_always ? 1 : 0;
         prm.offload_max = args->offload_max > 0 ? args->offload_max : kOffloadMax;
+        prm.tiers = (P.tiers && !P.root_qmask) ? 1 : 0;
         prm.root_qmask = P.root_qmask;
+        if (prm.tiers) {                         // where the thread tier starts
+            k_tier_bound<<<1, 32, 0, s>>>(args->root_split, P.n_roots, d_q + L);
+            TM_CUDA_TRY(cudaGetLastError());
+        }
         const SpecKernel *sk = (P.spec && !P.root_qmask) ? spec_kernel(tr, P.comine ? 0 : 1 + L) : nullptr;
         cudaError_t e;
         if (sk) {                                // the kernel compiled for this tree
@@ -348,6 +366,8 @@ int mine(const tm_graph *g, const tm_tree *tr, const tm_count_args *args, int64_
                                       16 * hs[kStHashProbe] + 4 * hs[kStPairProbe]);
         stats->tasks_split = (int64_t)hs[kStSplit];
         stats->algo_bytes_lists = (int64_t)(16 * hs[kStRoots] + 8 * hs[kStCand] + 12 * hs[kStLogDeg]);
+        stats->roots_thread_tier = (int64_t)hs[kStLaneRoots];
+        stats->roots_split = (int64_t)hs[kStSplitRoots];
         stats->idle_expired = idle_expired;
         const unsigned long long *hb = hs + kStatFields;
         stats->warp_imbalance = hb[kBusySum] ? (double)hb[kBusyMax] * (double)hb[kBusyWarps] / (double)hb[kBusySum] : 0.0;
@@ -616,7 +636,7 @@ extern "C" int tm_count_noalloc(const tm_graph *g, const tm_tree *tr, const int3
         TM_CUDA_TRY(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev));
         const int dyn_smem = (int)(sizeof(unsigned long long) * n_motifs);
         TM_TRY(allow_counter_smem());
-        TM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_mine<false>, kThreads, dyn_smem));
+        TM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_mine<false, false>, kThreads, dyn_smem));
         per_sm = std::max(per_sm, 1);
         const int blocks = n_sm * per_sm;
         Params prm{};                 // every field not set below is zero
@@ -643,8 +663,9 @@ extern "C" int tm_count_noalloc(const tm_graph *g, const tm_tree *tr, const int3
         prm.siblings = 0;
         prm.sib_always = 0;
         prm.offload_max = kOffloadMax;
+        prm.tiers = 0;
         prm.root_qmask = nullptr;
-        k_mine<false><<<blocks, kThreads, dyn_smem, s>>>(prm);
+        k_mine<false, false><<<blocks, kThreads, dyn_smem, s>>>(prm);
         TM_CUDA_TRY(cudaGetLastError());
     }
     k_to_i64<<<(n_motifs + 255) / 256, 256, 0, s>>>(d_cnt, counts, n_motifs);

@@ -274,8 +274,8 @@ __global__ void k_to_half(const float *w, __half *wh, int n) {
 }
 
 // descending predicted cost -> ascending key; split count from predicted work
-__global__ void k_plan_keys(const float *Y, int64_t n, float unit_log, int32_t max_split, uint32_t *key,
-                            int32_t *idx, int32_t *split) {
+__global__ void k_plan_keys(const float *Y, int64_t n, float unit_log, int32_t max_split, float thread_log,
+                            uint32_t *key, int32_t *idx, int32_t *split) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const float y = Y[i];
@@ -286,6 +286,7 @@ __global__ void k_plan_keys(const float *Y, int64_t n, float unit_log, int32_t m
     // slices of about exp(unit_log) predicted work each
     const float d = y - unit_log;
     int32_t sp = d <= 0.f ? 1 : (int32_t)fminf((float)max_split, ceilf(expf(fminf(d, 30.f))));
+    if (y < thread_log) sp = 0;                        // predicted light: the thread tier
     split[i] = sp;
 }
 
@@ -475,11 +476,12 @@ int tm_model_train(tm_model *m, const float *feats, const float *labels, int64_t
     return TM_OK;
 }
 
-int tm_plan(const tm_model *m, const float *feats, const int32_t *roots, int64_t n, double unit_work,
-            int32_t max_split, int32_t *roots_out, int32_t *split_out, void *stream) {
+namespace {
+int plan(const tm_model *m, const float *feats, const int32_t *roots, int64_t n, double unit_work, int32_t max_split,
+         double thread_work, int32_t *roots_out, int32_t *split_out, void *stream, const char *who) {
     if (!m || n < 0 || (n > 0 && (!feats || !roots || !roots_out || !split_out)) || !(unit_work >= 1.0) ||
-        max_split < 1) {
-        set_error("tm_plan: bad argument");
+        max_split < 1 || !(thread_work >= 0.0)) {
+        set_error(std::string(who) + ": bad argument");
         return TM_EINVAL;
     }
     if (n == 0) return TM_OK;
@@ -492,8 +494,10 @@ int tm_plan(const tm_model *m, const float *feats, const int32_t *roots, int64_t
     int32_t *idx = (int32_t *)(key + n);
     int32_t *split = idx + n;
     int rc = TM_OK;
+    // predictions are log1p(work); no root is below a threshold of 0
+    const float thread_log = thread_work > 0.0 ? (float)std::log1p(thread_work) : -INFINITY;
     k_mlp_fwd<<<grid(n, 128), 128, 0, s>>>(m->half, m->norm, feats, n, y);
-    k_plan_keys<<<grid(n), 256, 0, s>>>(y, n, (float)std::log(unit_work), max_split, key, idx, split);
+    k_plan_keys<<<grid(n), 256, 0, s>>>(y, n, (float)std::log(unit_work), max_split, thread_log, key, idx, split);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) { set_error(cudaGetErrorString(e)); rc = TM_ECUDA; }
     if (rc == TM_OK) rc = sort_u32_pairs(key, idx, n, 32, s);
@@ -504,6 +508,17 @@ int tm_plan(const tm_model *m, const float *feats, const int32_t *roots, int64_t
     }
     cudaFreeAsync(buf, s);
     return rc;
+}
+}  // namespace
+
+int tm_plan(const tm_model *m, const float *feats, const int32_t *roots, int64_t n, double unit_work,
+            int32_t max_split, int32_t *roots_out, int32_t *split_out, void *stream) {
+    return plan(m, feats, roots, n, unit_work, max_split, 0.0, roots_out, split_out, stream, "tm_plan");
+}
+
+int tm_plan_tiers(const tm_model *m, const float *feats, const int32_t *roots, int64_t n, double unit_work,
+                  int32_t max_split, double thread_work, int32_t *roots_out, int32_t *split_out, void *stream) {
+    return plan(m, feats, roots, n, unit_work, max_split, thread_work, roots_out, split_out, stream, "tm_plan_tiers");
 }
 
 }  // extern "C"

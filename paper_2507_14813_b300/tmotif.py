@@ -39,6 +39,7 @@ TM_SCHED_DYNAMIC = 0x100
 TM_SCHED_PLANNED = 0x200
 TM_GENERIC = 0x1000
 TM_SCHED_SIBLINGS = 0x400
+TM_SCHED_TIERS = 0x800
 TM_COMPILE_CHAINS = 0x1
 TM_COMPILE_CHECK = 0x2
 TM_SPEC_MAX_NODES = 256
@@ -130,7 +131,7 @@ class tm_run_stats(ctypes.Structure):
                 ("probes", ctypes.c_int64), ("leaf_evals", ctypes.c_int64), ("algo_bytes", ctypes.c_int64),
                 ("tasks_split", ctypes.c_int64), ("launches", ctypes.c_int64), ("kernel_ms", ctypes.c_double),
                 ("warp_imbalance", ctypes.c_double), ("algo_bytes_lists", ctypes.c_int64),
-                ("idle_expired", ctypes.c_int64)]
+                ("idle_expired", ctypes.c_int64), ("roots_thread_tier", ctypes.c_int64), ("roots_split", ctypes.c_int64)]
 
     def as_dict(self):
         return {name: getattr(self, name) for name, _ in self._fields_}
@@ -143,6 +144,7 @@ EXPORTS = ("tm_graph_load", "tm_graph_get_info", "tm_graph_edges", "tm_graph_fre
            "tm_graph_bipartite", "tm_comine_advice", "tm_enumerate",
            "tm_features", "tm_model_create", "tm_model_free", "tm_model_get_params", "tm_model_set_params",
            "tm_model_fit_norm", "tm_model_predict", "tm_model_loss_grad", "tm_model_train", "tm_plan",
+           "tm_plan_tiers",
            "tm_exec_create", "tm_exec_launch", "tm_exec_status", "tm_exec_free", "tm_autotune",
            "tm_server_open", "tm_server_submit", "tm_server_poll", "tm_server_get_info", "tm_server_close",
            "tm_last_error", "tm_version")
@@ -178,6 +180,7 @@ def lib():
         L.tm_model_loss_grad.argtypes = [P, P, P, i64, P, P, P]
         L.tm_model_train.argtypes = [P, P, P, i64, i32, i32, F, P, P]
         L.tm_plan.argtypes = [P, P, P, i64, ctypes.c_double, i32, P, P, P]
+        L.tm_plan_tiers.argtypes = [P, P, P, i64, ctypes.c_double, i32, ctypes.c_double, P, P, P]
         L.tm_exec_create.argtypes = [P, P, ctypes.POINTER(tm_count_args), P, P, ctypes.POINTER(P)]
         L.tm_exec_launch.argtypes = [P, P]
         L.tm_exec_status.argtypes = [P, P]
@@ -598,7 +601,16 @@ class Model:
                                     _stream(stream)))
         return hist[:epochs]
 
-    def plan(self, feats, roots, roots_out, split_out, unit_work: float, max_split: int, stream=None):
+    def plan(self, feats, roots, roots_out, split_out, unit_work: float, max_split: int, stream=None,
+             thread_work: float = 0.0):
+        """Order and slices (tm_plan); with thread_work > 0, roots predicted
+        below it get slice count 0: the thread tier of TM_SCHED_TIERS."""
+        if thread_work > 0:
+            _check(lib().tm_plan_tiers(self.h, _devf(feats, "feats"), _dev(roots, np.int32, "roots"), len(roots),
+                                       float(unit_work), int(max_split), float(thread_work),
+                                       _dev(roots_out, np.int32, "roots_out"), _dev(split_out, np.int32, "split_out"),
+                                       _stream(stream)))
+            return roots_out, split_out
         _check(lib().tm_plan(self.h, _devf(feats, "feats"), _dev(roots, np.int32, "roots"), len(roots),
                              float(unit_work), int(max_split), _dev(roots_out, np.int32, "roots_out"),
                              _dev(split_out, np.int32, "split_out"), _stream(stream)))
