@@ -116,7 +116,10 @@ constexpr long long kReadySpins = 1 << 22;  // bound on waiting for a claimed ta
 #endif
 constexpr long long kIdleSpins = 1 << 20;   // bound on an idle warp's wait for work
 
-enum : int8_t { kListOut = 0, kListIn = 1, kListGlobal = 2 };
+// candidate lists: out-list of a mapped source, in-list of a mapped
+// destination, the global edge window (neither mapped), or -- both mapped --
+// the run of edges between the two in the (src, dst) pair order
+enum : int8_t { kListOut = 0, kListIn = 1, kListGlobal = 2, kListPair = 3 };
 
 // A unit of work: the slice [lo, hi) of level k's candidate list of `node`,
 // under the partial match eid[0..k-1] (eid[0] is the root edge).  lo < 0
@@ -192,7 +195,8 @@ struct WarpState {
     int64_t end[kMaxE];       // end of the candidate slice
     int64_t cbase[kMaxE];     // start of the chunk held in cand[k]
     uint32_t mask[kMaxE];     // survivors of the held chunk not yet descended
-    int32_t lvert[kMaxE];     // list vertex (out/in lists)
+    int32_t lvert[kMaxE];     // list vertex (out/in lists; the source of a pair list)
+    int32_t lfar[kMaxE];      // pair lists: the mapped destination
     int32_t eid[kMaxE];       // matched edge id per level
     int64_t mpos[kMaxE];      // list position of the matched candidate
     int16_t node[kMaxE];
@@ -345,35 +349,94 @@ __device__ int64_t warp_upper(const int2 *__restrict__ adj, int64_t lo, int64_t 
     return b ? lo + (__ffs(b) - 1) : hi;
 }
 
+// The run of edges x -> w in the pair order: pair_eid[*st, *st + *len),
+// ascending edge ids (*len = 0 when there is none).
+__device__ __forceinline__ void pair_run(const DevGraph &g, int32_t x, int32_t w, int64_t *st, int64_t *len,
+                                         unsigned long long &hprobes) {
+    const unsigned long long key = ((unsigned long long)(uint32_t)x << 32) | (uint32_t)w;
+    uint64_t h = pair_hash(key) & g.pair_mask;
+    *st = 0;
+    *len = 0;
+    while (true) {
+        hprobes++;
+        const ulonglong2 e = __ldg(&g.pair_tab[h]);
+        if (e.x == key) {
+            *st = (int64_t)(e.y & 0xffffffffull);
+            *len = (int64_t)(e.y >> 32);
+            return;
+        }
+        if (e.x == kEmptyKey) return;
+        h = (h + 1) & g.pair_mask;
+    }
+}
+
+// first position in a[lo, hi) whose value exceeds key, galloping from lo; per lane
+__device__ __forceinline__ int64_t lane_gallop_e(const int32_t *__restrict__ a, int64_t lo, int64_t hi, int32_t key,
+                                                 unsigned long long &probes) {
+    if (lo >= hi) return lo;
+    probes++;
+    if (__ldg(a + lo) > key) return lo;
+    int64_t x = lo, step = 1, y = hi;          // a[x] <= key; answer in (x, y]
+    while (true) {
+        const int64_t q = x + step;
+        if (q >= hi) break;
+        probes++;
+        if (__ldg(a + q) <= key) { x = q; step <<= 1; } else { y = q; break; }
+    }
+    while (y - x > 1) {
+        const int64_t mid = x + ((y - x) >> 1);
+        probes++;
+        if (__ldg(a + mid) <= key) x = mid; else y = mid;
+    }
+    return y;
+}
+
+// first position in a[lo, hi) whose value exceeds key; warp-cooperative (int32 arrays)
+__device__ int64_t warp_upper_e(const int32_t *__restrict__ a, int64_t lo, int64_t hi, int32_t key, int lane,
+                                unsigned long long &probes) {
+    while (hi - lo > 32) {
+        const int64_t step = (hi - lo + 31) >> 5;
+        int64_t q = lo + (int64_t)(lane + 1) * step - 1;
+        if (q > hi - 1) q = hi - 1;
+        const bool gt = __ldg(a + q) > key;
+        probes += 1;
+        const uint32_t b = __ballot_sync(0xffffffffu, gt);
+        if (b == 0) return hi;
+        const int f = __ffs(b) - 1;
+        const int64_t qf = __shfl_sync(0xffffffffu, q, f);
+        const int64_t qp = __shfl_sync(0xffffffffu, q, f > 0 ? f - 1 : 0);
+        lo = f > 0 ? qp + 1 : lo;
+        hi = qf;
+    }
+    const int64_t q = lo + lane;
+    const bool gt = q < hi && __ldg(a + q) > key;
+    probes += q < hi;
+    const uint32_t b = __ballot_sync(0xffffffffu, gt);
+    return b ? lo + (__ffs(b) - 1) : hi;
+}
+
 // |edges x -> w with lo < eid <= hi|
 __device__ int64_t pair_count(const DevGraph &g, int32_t x, int32_t w, int32_t lo, int32_t hi,
                               unsigned long long &hprobes, unsigned long long &pprobes) {
     if (hi <= lo) return 0;
-    unsigned long long key = ((unsigned long long)(uint32_t)x << 32) | (uint32_t)w;
-    uint64_t h = pair_hash(key) & g.pair_mask;
-    while (true) {
-        hprobes++;
-        ulonglong2 e = __ldg(&g.pair_tab[h]);
-        if (e.x == key) {
-            int64_t st = (int64_t)(e.y & 0xffffffffull);
-            int64_t len = (int64_t)(e.y >> 32);
-            const int32_t *run = g.pair_eid + st;
-            if (len <= 16) {
-                int64_t c = 0;
-                for (int64_t i = 0; i < len; i++) {
-                    int32_t v = __ldg(run + i);
-                    c += (v > lo) & (v <= hi);
-                }
-                pprobes += len;
-                return c;
-            }
-            int64_t a = lane_upper_e(run, 0, len, lo, pprobes);
-            int64_t b = lane_upper_e(run, a, len, hi, pprobes);
-            return b - a;
+    int64_t st, len;
+    pair_run(g, x, w, &st, &len, hprobes);
+    if (len == 0) return 0;
+    const int32_t *run = g.pair_eid + st;
+    if (len <= 16) {
+        int64_t c = 0;
+        for (int64_t i = 0; i < len; i++) {
+            int32_t v = __ldg(run + i);
+            c += (v > lo) & (v <= hi);
         }
-        if (e.x == kEmptyKey) return 0;
-        h = (h + 1) & g.pair_mask;
+        pprobes += len;
+        return c;
     }
+    // the window (lo, hi] is short against a run over the whole time span:
+    // binary search for its start, gallop from there for its end
+    const int64_t a = lane_upper_e(run, 0, len, lo, pprobes);
+    const int64_t b = lane_gallop_e(run, a, len, hi, pprobes);
+    return b - a;
 }
 
 __device__ __forceinline__ int vload(const int *p) { return *(volatile const int *)p; }
@@ -574,7 +637,7 @@ struct Miner {
         const int uk = N.eu[k], vk = N.ev[k];
         int32_t cs, cd;
         const int8_t lt = ws.ltype[k];
-        if (lt == kListOut) { cs = ws.lvert[k]; cd = c.x; }
+        if (lt == kListOut || lt == kListPair) { cs = ws.lvert[k]; cd = c.x; }
         else if (lt == kListIn) { cs = c.x; cd = ws.lvert[k]; }
         else {                                             // the root edge, or a global-window level
             const bool mine = (S >> lane) & 1u;
@@ -607,16 +670,13 @@ struct Miner {
     }
 
     // Candidate list of level k of node N under the current mapping.
-    __device__ __forceinline__ void list_of(const DevNode &N, int k, int8_t &lt, int32_t &x) const {
+    __device__ __forceinline__ void list_of(const DevNode &N, int k, int8_t &lt, int32_t &x, int32_t &far) const {
         const int u = N.eu[k], v = N.ev[k], nv = N.nvb[k];
         const bool um = u < nv, vm = v < nv;
         x = 0;
-        if (um && vm) {
-            int32_t xu = ws.m2g[u], xv = ws.m2g[v];
-            int64_t du = __ldg(p.g.out_off + xu + 1) - __ldg(p.g.out_off + xu);
-            int64_t dv = __ldg(p.g.in_off + xv + 1) - __ldg(p.g.in_off + xv);
-            if (du <= dv) { lt = kListOut; x = xu; } else { lt = kListIn; x = xv; }
-        } else if (um) { lt = kListOut; x = ws.m2g[u]; }
+        far = 0;
+        if (um && vm) { lt = kListPair; x = ws.m2g[u]; far = ws.m2g[v]; }   // exactly the x -> far edges
+        else if (um) { lt = kListOut; x = ws.m2g[u]; }
         else if (vm) { lt = kListIn; x = ws.m2g[v]; }
         else { lt = kListGlobal; }
     }
@@ -725,6 +785,16 @@ struct Miner {
         return n;
     }
 
+    // End of a pair run's window: run[rel..len) relative to base b0, the first
+    // position whose edge id exceeds hi; one lane gallops, the warp gets it.
+    __device__ int64_t lane_gallop_warp(int64_t rel, int64_t len, int64_t b0, int32_t hi) {
+        int64_t r = 0;
+        unsigned long long pr = 0;
+        if (lane == 0) r = lane_gallop_e(p.g.pair_eid + b0, rel, len, hi, pr);
+        if (kStats && lane == 0) w.v[kStPairProbe] += pr;
+        return __shfl_sync(0xffffffffu, r, 0);
+    }
+
     // Open level k for node `node` (siblings up to sib_end): the slice of
     // its list with edge ids in (eid[k-1], ehi].
     __device__ void open(int k, int node, int sib_end) {
@@ -741,13 +811,24 @@ struct Miner {
         const int32_t last = ws.eid[k - 1];
         const int32_t hi = frame_hi(N);
         int8_t lt;
-        int32_t x;
-        list_of(N, k, lt, x);
+        int32_t x, far;
+        list_of(N, k, lt, x, far);
         int64_t start, end;
         int64_t deg = p.g.E;                            // length of the list searched
         if (kHasGlobal && lt == kListGlobal) {
             start = (int64_t)last + 1;
             end = (int64_t)hi + 1;
+        } else if (lt == kListPair) {                   // both endpoints mapped: the x -> far run
+            int64_t st = 0, len = 0;
+            unsigned long long hp = 0;
+            if (lane == 0) pair_run(p.g, x, far, &st, &len, hp);
+            st = __shfl_sync(0xffffffffu, st, 0);
+            len = __shfl_sync(0xffffffffu, len, 0);
+            if (kStats && lane == 0) w.v[kStHashProbe] += hp;
+            const int64_t b0 = st, b1 = st + len;
+            deg = len;
+            start = (len <= 32) ? b0 : warp_upper_e(p.g.pair_eid, b0, b1, last, lane, w.v[kStPairProbe]);
+            end = (b1 - start <= 32) ? b1 : b0 + lane_gallop_warp(start - b0, b1 - b0, b0, hi);
         } else {
             const int64_t *off = lt == kListOut ? p.g.out_off : p.g.in_off;
             const int2 *adj = lt == kListOut ? p.g.out_adj : p.g.in_adj;
@@ -760,7 +841,8 @@ struct Miner {
             else start = warp_upper(adj, b0, b1, last, lane, w.v[kStListProbe]);
             end = (b1 - start <= 32) ? b1 : warp_gallop(adj, start, b1, hi, lane, w.v[kStListProbe]);
         }
-        const bool star = lt != kListGlobal && star_of(N, k);
+        const bool star = (lt == kListOut || lt == kListIn) && star_of(N, k);
+        if (lane == 0) ws.lfar[k] = far;
         set_frame(k, node, sib_end, lt, x, start, end, seq_of(N, k), end, star, 0);
         if (star) {
             int8_t sm = kSameGallop;
@@ -1045,12 +1127,13 @@ struct Miner {
     }
 
     // This lane's entry of the chunk of level k starting at `base` (lists end at `end`).
-    __device__ __forceinline__ int2 fetch(int8_t lt, int64_t base, int64_t end) const {
+    __device__ __forceinline__ int2 fetch(int8_t lt, int64_t base, int64_t end, int32_t far) const {
         const int64_t i = base + lane;
         int2 c = make_int2(0, 0);
         if (i < end) {
             if (lt == kListOut) c = __ldg(&p.g.out_adj[i]);
             else if (lt == kListIn) c = __ldg(&p.g.in_adj[i]);
+            else if (lt == kListPair) c = make_int2(far, __ldg(p.g.pair_eid + i));
             else if (kHasGlobal) c = make_int2(0, (int32_t)i);
         }
         return c;
@@ -1081,7 +1164,7 @@ struct Miner {
             for (int l = 0; l < kMaxV; l++) bad |= (l < nv) & ((s == ws.m2g[l]) | (d == ws.m2g[l]));
             ok = !bad;
         } else if (um && vm) {
-            ok = c.x == (lt == kListOut ? ws.m2g[v] : ws.m2g[u]);
+            ok = lt == kListPair || c.x == (lt == kListOut ? ws.m2g[v] : ws.m2g[u]);
         } else {
             bool bad = false;
 #pragma unroll
@@ -1116,7 +1199,7 @@ struct Miner {
     __device__ void load_chunk(int k) {
         const int64_t base = chunk_base(k);
         const int64_t end = ws.end[k];
-        step(k, base, end, fetch(ws.ltype[k], base, end));
+        step(k, base, end, fetch(ws.ltype[k], base, end, ws.lfar[k]));
     }
 
     // The hot case of drain: a counting-only star frame whose work per
@@ -1251,7 +1334,8 @@ struct Miner {
         const int8_t lt = ws.ltype[k];
         int64_t base = chunk_base(k);
         int64_t end = ws.end[k];
-        int2 c = fetch(lt, base, end);
+        const int32_t far = ws.lfar[k];
+        int2 c = fetch(lt, base, end, far);
         // a star frame counting one star leaf with one ref: sum that ref's
         // counts in registers across chunks and add them once
         const DevNode &N = TM_NODE(ws.node[k]);
@@ -1281,7 +1365,7 @@ struct Miner {
             if (more) {
                 nbase = chunk_base(k);
                 nend = ws.end[k];
-                nc = fetch(lt, nbase, nend);
+                nc = fetch(lt, nbase, nend, far);
             }
             step(k, base, end, c);
             if (!more || ws.pos[k] >= ws.end[k]) break;   // done, or the window ended in this chunk
@@ -1309,7 +1393,7 @@ struct Miner {
                 const DevNode &N = TM_NODE(ws.node[k]);
                 const int8_t lt = ws.ltype[k];
                 int32_t cs, cd;
-                if (lt == kListOut) { cs = ws.lvert[k]; cd = cj.x; }
+                if (lt == kListOut || lt == kListPair) { cs = ws.lvert[k]; cd = cj.x; }
                 else if (lt == kListIn) { cs = cj.x; cd = ws.lvert[k]; }
                 else { cs = __ldg(g.src + cj.y); cd = __ldg(g.dst + cj.y); }   // root edge or global window
                 __syncwarp();
@@ -1575,10 +1659,13 @@ struct Miner {
             return;
         }
         int8_t lt;
-        int32_t x;
-        list_of(N, k, lt, x);
-        const bool star = lt != kListGlobal && star_of(N, k);
-        if (lane == 0) ws.cache_owner = -1;
+        int32_t x, far;
+        list_of(N, k, lt, x, far);
+        const bool star = (lt == kListOut || lt == kListIn) && star_of(N, k);
+        if (lane == 0) {
+            ws.cache_owner = -1;
+            ws.lfar[k] = far;
+        }
         __syncwarp();
         if (star) cache_claim(k);
         // a top-down slice needs the survivors above it, up to the window's end
