@@ -211,6 +211,11 @@ struct WarpState {
     // (endpoint << 32) | survivors with that endpoint scanned so far
     unsigned long long cslot[kSlots];
     int32_t cache_owner;      // level whose star frame owns cslot, or -1
+    // the last uniform pair window (leaf_batch): key (source, destination),
+    // (window end, frame start); the run's start and the window [wlo, whi) in it
+    unsigned long long pc_k1, pc_k2;
+    int64_t pc_st;
+    int32_t pc_wlo, pc_whi;
     int32_t m2g[kMaxV];
     int32_t ehi[TM_MAX_DELTAS];
 };
@@ -581,17 +586,64 @@ struct Miner {
     // the later survivors of level k (suffix count `suf` of the chunk) minus
     // the later edges of the lane's own (src, dst) run inside the window.
     // S: lanes that evaluate; Sall: every survivor of the chunk (for the star count).
+    // The leaf edge's two endpoints were mapped before level k, so every lane
+    // counts edges of one pair, xu -> xv, in (its candidate, hi]: lane 0 finds
+    // the run and the part of it inside (eid[k-1], hi] once (cached per warp
+    // while the pair, the window end and the frame start stay the same), and
+    // each lane searches only that part.
+    __device__ void uniform_pair_window(const DevNode &L, int lv, int k, int32_t hi, const int32_t **run,
+                                        int32_t *wlo, int32_t *whi) {
+        const int32_t xu = ws.m2g[L.eu[lv]], xv = ws.m2g[L.ev[lv]];
+        const int32_t flast = ws.eid[k - 1];
+        const unsigned long long k1 = (unsigned long long)(uint32_t)xu | ((unsigned long long)(uint32_t)xv << 32);
+        const unsigned long long k2 = (unsigned long long)(uint32_t)hi | ((unsigned long long)(uint32_t)flast << 32);
+        __syncwarp();
+        if (lane == 0 && (ws.pc_k1 != k1 || ws.pc_k2 != k2)) {
+            int64_t st, len;
+            unsigned long long hp = 0, pp = 0;
+            pair_run(p.g, xu, xv, &st, &len, hp);
+            const int32_t *r = p.g.pair_eid + st;
+            const int64_t a = lane_upper_e(r, 0, len, flast, pp);
+            const int64_t b = lane_gallop_e(r, a, len, hi, pp);
+            ws.pc_k1 = k1;
+            ws.pc_k2 = k2;
+            ws.pc_st = st;
+            ws.pc_wlo = (int32_t)a;
+            ws.pc_whi = (int32_t)b;
+            if (kStats) {
+                w.v[kStHashProbe] += hp;
+                w.v[kStPairProbe] += pp;
+            }
+        }
+        __syncwarp();
+        *run = p.g.pair_eid + ws.pc_st;
+        *wlo = ws.pc_wlo;
+        *whi = ws.pc_whi;
+    }
+
     __device__ void leaf_batch(const DevNode &L, int k, uint32_t S, int uk, int vk, int32_t cs, int32_t cd,
                                int32_t last, int32_t fhi, int64_t suf, int32_t y, uint32_t peers, uint32_t Sall) {
         const bool star = (L.flags & kNodeStarLeaf) && ws.star[k];
         const uint32_t above = (lane == 31) ? 0u : ~((2u << lane) - 1u);       // lanes after this one
+        const int lv = k + 1;
+        const bool uni = k >= 1 && L.eu[lv] < L.nvb[k] && L.ev[lv] < L.nvb[k];   // same pair for every lane
         for (int i = 0; i < L.n_ref; i++) {
             const DevRef ref = TM_REF(L.ref_begin + i);
             if (!((rmask >> ref.query) & 1ull)) continue;
             const int32_t hi = ehi(ref.delta);
             unsigned long long c = 0;
+            const int32_t *urun = nullptr;
+            int32_t uwlo = 0, uwhi = 0;
+            if (uni) uniform_pair_window(L, lv, k, hi, &urun, &uwlo, &uwhi);
             if (((S >> lane) & 1u) && last < hi) {
-                if (star && hi == fhi) {
+                if (uni) {
+                    unsigned long long pp = 0;
+                    c = (unsigned long long)(uwhi - lane_upper_e(urun, uwlo, uwhi, last, pp));
+                    if (kStats) {
+                        w.v[kStPairProbe] += pp;
+                        w.v[kStLeaf] += 1;
+                    }
+                } else if (star && hi == fhi) {
                     unsigned long long pr = 0;
                     const int64_t later = suf + __popc(Sall & above);
                     int64_t same;
@@ -1448,7 +1500,10 @@ struct Miner {
         const int32_t a = __ldg(g.src + r), b = __ldg(g.dst + r);
         if (a == b) return;                             // injective map needs a != b
         windows(r);
-        if (lane == 0) ws.cache_owner = -1;
+        if (lane == 0) {
+            ws.cache_owner = -1;
+            ws.pc_k1 = ~0ull;                           // no uniform pair window cached
+        }
         const DevNode &N0 = TM_NODE(0);
         set_frame(0, 0, 1, kListGlobal, -1, 0, 0, seq_of(N0, 0), 0, false, 0);
         if (lane == 0) ws.cbase[0] = r;
@@ -1707,6 +1762,8 @@ __global__ void __launch_bounds__(kThreads, TM_MIN_BLOCKS) k_mine(Params p) {
     for (int i = threadIdx.x; i < n_smem; i += blockDim.x) s_cnt[i] = 0;
     __syncthreads();
     Miner<kStats, kExt> M(p, s_ws[warp], s_cnt + (p.smem_counters == 2 ? warp * n_cnt : 0), lane);
+    if (lane == 0) s_ws[warp].pc_k1 = ~0ull;            // no uniform pair window cached yet
+    __syncwarp();
     if (p.dynamic && lane == 0) atomicAdd(&p.q->busy, 1);
     // stats launch: this warp's cycles spent other than waiting for work
     const long long t_begin = kStats ? clock64() : 0;
