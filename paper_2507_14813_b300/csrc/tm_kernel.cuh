@@ -1291,10 +1291,11 @@ struct Miner {
         const int8_t sm = ws.same_mode[k];
         const bool own = ws.cache_owner == k;
         const uint32_t above = (lane == 31) ? 0u : ~((2u << lane) - 1u);
-        int64_t pos = ws.pos[k], end = ws.end[k], suf = ws.suf[k];
-        const int64_t suf0 = suf;
+        // positions and counts fit 32 bits (lists and windows below 2^31 entries)
+        int32_t pos = (int32_t)ws.pos[k], end = (int32_t)ws.end[k], suf = (int32_t)ws.suf[k];
+        const int32_t suf0 = suf;
         unsigned long long acc_l = 0;
-        int64_t cb = max(pos, end - 32), ce = end;       // the chunk [cb, ce), scanned from the top
+        int32_t cb = max(pos, end - 32), ce = end;       // the chunk [cb, ce), scanned from the top
         int2 c = (cb + lane < ce) ? __ldg(adj + cb + lane) : make_int2(0, 0);
         while (true) {
             end = cb;                                    // claimed: a donation cannot hand it out
@@ -1307,10 +1308,10 @@ struct Miner {
                 }
                 __syncwarp();
                 maybe_donate(kbase, k);
-                pos = ws.pos[k];                         // a donation hands over the bottom part
+                pos = (int32_t)ws.pos[k];                // a donation hands over the bottom part
             }
             const bool more = pos < end;
-            int64_t nb = 0;
+            int32_t nb = 0;
             int2 nc = make_int2(0, 0);
             if (more) {
                 nb = max(pos, end - 32);
@@ -1325,8 +1326,8 @@ struct Miner {
             const uint32_t peers = (sm != kSameGallop) ? __match_any_sync(0xffffffffu, ok ? c.x : -1) : 0u;
             int32_t known = -1;
             if (ok) {
-                const int64_t later = suf + __popc(S & above);
-                int64_t same;
+                const int32_t later = suf + __popc(S & above);
+                int32_t same;
                 if (sm == kSameChunk) {
                     same = __popc(peers & above);
                 } else {
@@ -1334,17 +1335,17 @@ struct Miner {
                     const unsigned long long ent = sm == kSameTable ? ws.cslot[slot] : 0ull;
                     const uint32_t key = (uint32_t)(ent >> 32);
                     if (sm == kSameTable && key == (uint32_t)c.x) {
-                        same = (int64_t)(uint32_t)ent + __popc(peers & above);
+                        same = (int32_t)(uint32_t)ent + __popc(peers & above);
                     } else if (sm == kSameTable && key == kCacheEmpty) {
                         same = __popc(peers & above);    // a value seen above would have claimed the slot
                     } else {
                         unsigned long long pr = 0;
-                        same = run_tail(p.g.pair_eid, __ldg(p.g.pr_pos + c.y), __ldg(p.g.pr_end + c.y), fhi, pr);
+                        same = (int32_t)run_tail(p.g.pair_eid, __ldg(p.g.pr_pos + c.y), __ldg(p.g.pr_end + c.y), fhi, pr);
                         if (kStats) w.v[kStPairProbe] += pr + 2;
                     }
                 }
-                acc_l += (unsigned long long)(later - same);
-                known = (int32_t)same;
+                acc_l += (unsigned long long)(uint32_t)(later - same);
+                known = same;
                 if (kStats) w.v[kStLeaf] += 1;
             }
             if (kStats) {
