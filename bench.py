@@ -780,6 +780,9 @@ def main():
                      "warp": st_t["n_roots"] - st_t["roots_thread_tier"] - st_t["roots_split"]}
     # the same step, static: one warp per root, no plan, no queue
     static = timed(mode & ~tmotif.TM_SCHED_DYNAMIC, False, n_cmp) if args.with_static and not args.static else None
+    # the per-motif comparator with static scheduling too
+    perm_static = (timed((mode & ~tmotif.TM_SCHED_DYNAMIC) | tmotif.TM_PERMOTIF, False, n_cmp)
+                   if args.with_static and not args.static and not args.no_permotif else None)
 
     # per-motif comparator on the same roots (one chain tree per motif), same schedule
     perm = perm_reactive = None
@@ -850,7 +853,7 @@ def main():
         "specialised_speedup_vs_generic": (generic / ms_step) if generic else None,
         "siblings_ms_per_step": siblings,
         "tiers_ms_per_step": tiers, "thread_work": args.thread_work, "tier_histogram": tier_hist,
-        "static_ms_per_step": static,
+        "static_ms_per_step": static, "permotif_static_ms_per_step": perm_static,
         "schedule_siblings": "the same step with sibling splitting and multi-offload (TM_SCHED_SIBLINGS)",
         "permotif_ms_per_step": perm,
         "comine_speedup_vs_permotif": (perm / ms_step) if perm else None,

@@ -16,7 +16,7 @@ pytestmark = pytest.mark.gpu
 def _pool_high_water():
     """Used-memory high-water mark of the device's default memory pool (the
     pool cudaMallocAsync draws from), reset to the current use first; None
-    when the driver bindings are missing."""
+    when the CUDA driver API bindings are missing."""
     try:
         from cuda.bindings import driver as cu
     except ImportError:
