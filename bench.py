@@ -121,7 +121,7 @@ class ClockSampler:
 # source reports null.  dram_bytes = dram__bytes_read.sum +
 # dram__bytes_write.sum; l2_pct / dram_pct = ncu's L2 and DRAM throughput
 # (percent of peak sustained).
-PROFILE = {"2caac79c21c0df8c": {"learned": {"dram_bytes": 335.1e6, "l2_pct": 6.16, "dram_pct": 0.0115}}}
+PROFILE = {"10da3a1e2779eb87": {"learned": {"dram_bytes": 334.66e6, "l2_pct": 6.12, "dram_pct": 0.01}}}
 
 
 def kernel_hash():

@@ -97,8 +97,10 @@ def build(force: bool = False, verbose: bool = False, variant=None) -> str:
             os.replace(o + ".tmp", o)
         return o
 
+    # the mining kernel's instantiations take minutes each: start them first
+    order = sorted(sources(), key=lambda p: not os.path.basename(p).startswith("tm_kmine_"))
     with concurrent.futures.ThreadPoolExecutor(max_workers=max(1, min(8, os.cpu_count() or 1))) as ex:
-        objs = list(ex.map(obj, sources()))
+        objs = list(ex.map(obj, order))
     tmp = lib + ".tmp%d" % os.getpid()
     cuda_lib = os.path.join(os.path.dirname(os.path.dirname(shutil.which(nvcc) or "/usr/local/cuda/bin/nvcc")),
                             "lib64")

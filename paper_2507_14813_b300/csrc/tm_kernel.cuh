@@ -237,7 +237,7 @@ __device__ __forceinline__ int64_t sat_add(int64_t a, int64_t b) {
 }
 
 // last edge id e >= r with t[e] <= limit (t[r] <= limit holds); serial, per lane
-__device__ int32_t window_end(const int64_t *__restrict__ t, int64_t E, int32_t r, int64_t limit, unsigned long long &probes) {
+static __device__ int32_t window_end(const int64_t *__restrict__ t, int64_t E, int32_t r, int64_t limit, unsigned long long &probes) {
     int64_t lo = r, step = 1;          // t[lo] <= limit
     int64_t hi = E;                    // t[hi] > limit or hi == E
     while (true) {                     // gallop
@@ -311,12 +311,12 @@ __device__ __forceinline__ int64_t after_pos(const DevGraph &g, bool out, int32_
 }
 
 // first position in adj[lo, hi) whose edge id exceeds key; warp-cooperative
-__device__ int64_t warp_upper(const int2 *__restrict__ adj, int64_t lo, int64_t hi, int32_t key, int lane,
+static __device__ int64_t warp_upper(const int2 *__restrict__ adj, int64_t lo, int64_t hi, int32_t key, int lane,
                               unsigned long long &probes);
 
 // the same, galloping from lo: one round of probes at lo + 2^lane - 1 brackets
 // the answer, then the 32-ary search narrows it
-__device__ int64_t warp_gallop(const int2 *__restrict__ adj, int64_t lo, int64_t hi, int32_t key, int lane,
+static __device__ int64_t warp_gallop(const int2 *__restrict__ adj, int64_t lo, int64_t hi, int32_t key, int lane,
                                unsigned long long &probes) {
     if (hi - lo <= 32) return warp_upper(adj, lo, hi, key, lane, probes);
     int64_t q = lane == 31 ? hi - 1 : lo + ((int64_t)1 << lane) - 1;
@@ -331,7 +331,7 @@ __device__ int64_t warp_gallop(const int2 *__restrict__ adj, int64_t lo, int64_t
     return warp_upper(adj, f > 0 ? qp + 1 : lo, qf, key, lane, probes) ;
 }
 
-__device__ int64_t warp_upper(const int2 *__restrict__ adj, int64_t lo, int64_t hi, int32_t key, int lane,
+static __device__ int64_t warp_upper(const int2 *__restrict__ adj, int64_t lo, int64_t hi, int32_t key, int lane,
                               unsigned long long &probes) {
     while (hi - lo > 32) {
         int64_t step = (hi - lo + 31) >> 5;
@@ -397,7 +397,7 @@ __device__ __forceinline__ int64_t lane_gallop_e(const int32_t *__restrict__ a, 
 }
 
 // first position in a[lo, hi) whose value exceeds key; warp-cooperative (int32 arrays)
-__device__ int64_t warp_upper_e(const int32_t *__restrict__ a, int64_t lo, int64_t hi, int32_t key, int lane,
+static __device__ int64_t warp_upper_e(const int32_t *__restrict__ a, int64_t lo, int64_t hi, int32_t key, int lane,
                                 unsigned long long &probes) {
     while (hi - lo > 32) {
         const int64_t step = (hi - lo + 31) >> 5;
@@ -421,7 +421,7 @@ __device__ int64_t warp_upper_e(const int32_t *__restrict__ a, int64_t lo, int64
 }
 
 // |edges x -> w with lo < eid <= hi|
-__device__ int64_t pair_count(const DevGraph &g, int32_t x, int32_t w, int32_t lo, int32_t hi,
+static __device__ int64_t pair_count(const DevGraph &g, int32_t x, int32_t w, int32_t lo, int32_t hi,
                               unsigned long long &hprobes, unsigned long long &pprobes) {
     if (hi <= lo) return 0;
     int64_t st, len;
@@ -1870,24 +1870,6 @@ __global__ void __launch_bounds__(kThreads, TM_MIN_BLOCKS) k_mine(Params p) {
                 for (int wi = 1; wi < kWarps; wi++) c += s_cnt[wi * n_cnt + i];
             if (c) atomicAdd(&p.counts[i], c);
         }
-}
-
-// The thread tier's first root: the tail of a planned order whose slice
-// count is 0 (the plan marks roots predicted light so; counts are
-// non-increasing along the order, found by binary search).
-__global__ void k_tier_bound(const int32_t *split, int64_t n, QueueHdr *q) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    int64_t lo = 0, hi = n;
-    while (lo < hi) {
-        const int64_t mid = lo + (hi - lo) / 2;
-        if (split[mid] > 0) lo = mid + 1; else hi = mid;
-    }
-    q->lane_from = lo;
-}
-
-__global__ void k_to_i64(const unsigned long long *a, int64_t *b, int n) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) b[i] = (int64_t)a[i];
 }
 
 }  // namespace dev

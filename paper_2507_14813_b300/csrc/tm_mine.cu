@@ -1,6 +1,7 @@
 // Host side of counting: launch planning, scratch, the table-driven kernel
 // and its entry points (tm_count, replay, autotuning, allocation-free
-// counting).  The kernel itself is tm_kernel.cuh.
+// counting).  The kernel itself is tm_kernel.cuh; its four instantiations
+// are compiled in tm_kmine_*.cu.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -9,12 +10,30 @@
 
 #include "tm_codegen.h"
 #include "tm_internal.h"
-#include "tm_kernel.cuh"
+#include "tm_instances.h"
 
 namespace tmo {
 using namespace dev;
 
 namespace {
+
+// The thread tier's first root: the tail of a planned order whose slice
+// count is 0 (the plan marks roots predicted light so; counts are
+// non-increasing along the order, found by binary search).
+__global__ void k_tier_bound(const int32_t *split, int64_t n, QueueHdr *q) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    int64_t lo = 0, hi = n;
+    while (lo < hi) {
+        const int64_t mid = lo + (hi - lo) / 2;
+        if (split[mid] > 0) lo = mid + 1; else hi = mid;
+    }
+    q->lane_from = lo;
+}
+
+__global__ void k_to_i64(const unsigned long long *a, int64_t *b, int n) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) b[i] = (int64_t)a[i];
+}
 
 __global__ void k_status(const QueueHdr *q, int n_launch, int32_t *status) {
     int e = 0;
@@ -30,10 +49,10 @@ int allow_counter_smem() {
     TM_CUDA_TRY(cudaGetDevice(&dev));
     if (dev >= 0 && dev < 64 && done[dev]) return TM_OK;
     const int bytes = (int)(sizeof(unsigned long long) * kSmemCounters);
-    TM_CUDA_TRY(cudaFuncSetAttribute(k_mine<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
-    TM_CUDA_TRY(cudaFuncSetAttribute(k_mine<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
-    TM_CUDA_TRY(cudaFuncSetAttribute(k_mine<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
-    TM_CUDA_TRY(cudaFuncSetAttribute(k_mine<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+    TM_CUDA_TRY(cudaFuncSetAttribute(mine_kernel<false, false>(), cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+    TM_CUDA_TRY(cudaFuncSetAttribute(mine_kernel<true, false>(), cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+    TM_CUDA_TRY(cudaFuncSetAttribute(mine_kernel<false, true>(), cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+    TM_CUDA_TRY(cudaFuncSetAttribute(mine_kernel<true, true>(), cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
     if (dev >= 0 && dev < 64) done[dev] = 1;
     return TM_OK;
 }
@@ -56,11 +75,10 @@ struct Plan {
     size_t o_q = 0, o_tasks = 0, o_ready = 0, bytes = 0, b_ready = 0;
 };
 
-// The table-driven kernel for a launch: stats or not, thread tier or not.
-using MineKernel = void (*)(Params);
+// The table-driven kernel for a launch: stats or not, extended schedules or not.
 MineKernel kernel_of(bool stats, bool ext) {
-    if (ext) return stats ? k_mine<true, true> : k_mine<false, true>;
-    return stats ? k_mine<true, false> : k_mine<false, false>;
+    if (ext) return stats ? mine_kernel<true, true>() : mine_kernel<false, true>();
+    return stats ? mine_kernel<true, false>() : mine_kernel<false, false>();
 }
 
 // roots a warp claims at a time: 1, or up to 16 when there are many roots per warp
@@ -636,7 +654,7 @@ extern "C" int tm_count_noalloc(const tm_graph *g, const tm_tree *tr, const int3
         TM_CUDA_TRY(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev));
         const int dyn_smem = (int)(sizeof(unsigned long long) * n_motifs);
         TM_TRY(allow_counter_smem());
-        TM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_mine<false, false>, kThreads, dyn_smem));
+        TM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, mine_kernel<false, false>(), kThreads, dyn_smem));
         per_sm = std::max(per_sm, 1);
         const int blocks = n_sm * per_sm;
         Params prm{};                 // every field not set below is zero
@@ -665,7 +683,7 @@ extern "C" int tm_count_noalloc(const tm_graph *g, const tm_tree *tr, const int3
         prm.offload_max = kOffloadMax;
         prm.tiers = 0;
         prm.root_qmask = nullptr;
-        k_mine<false, false><<<blocks, kThreads, dyn_smem, s>>>(prm);
+        mine_kernel<false, false>()<<<blocks, kThreads, dyn_smem, s>>>(prm);
         TM_CUDA_TRY(cudaGetLastError());
     }
     k_to_i64<<<(n_motifs + 255) / 256, 256, 0, s>>>(d_cnt, counts, n_motifs);
