@@ -34,14 +34,15 @@
 // expired wait sets an error flag that the host turns into TM_ETIMEOUT.
 //
 // This file is the kernel alone.  The library compiles it once as the
-// table-driven kernel (tm_mine.cu): the MG-Tree is read from a node table in
-// device memory and every array is sized to the library's limits.  For one
-// tree the library can also compile it at run time (NVRTC, tm_codegen.cpp)
-// behind a generated prelude that defines TM_K_SPEC: the node, ref and
-// window tables are then constant data of the kernel, the tree's counts and
-// properties are compile-time constants, and arrays and label loops are
-// sized to the tree's depth and vertex count (the code generation of
-// Section 5.1, "GPU Code-generation").
+// table-driven kernel (tm_kmine_*.cu, launched from tm_mine.cu): the
+// MG-Tree is read from a node table in device memory and every array is
+// sized to the library's limits.  For one tree the library can also
+// compile it at run time (NVRTC, tm_codegen.cpp) behind a generated
+// prelude that defines TM_K_SPEC: the node, ref and window tables are then
+// constant data of the kernel, the tree's counts and properties are
+// compile-time constants, and arrays and label loops are sized to the
+// tree's depth and vertex count (the code generation of Section 5.1, "GPU
+// Code-generation").
 #pragma once
 
 #include "tm_device.h"
