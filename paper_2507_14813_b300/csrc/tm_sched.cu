@@ -11,7 +11,10 @@
 //   k_mlp_fwd    8 -> 64 -> 64 -> 1 perceptron, ReLU, FP16 weights, FP32
 //                accumulation, standardised inputs;
 //   k_mlp_grad   the mean-squared-error gradient of a minibatch (chain rule,
-//                one thread per sample, FP32 accumulation);
+//                one thread per sample, FP32 accumulation) into per-block
+//                partial sums, which k_grad_sum adds in block order: no
+//                floating-point atomics, so training is reproducible run to
+//                run (and with it the plan);
 //   k_adam       Adam on FP32 master weights, refreshing the FP16 copy;
 //   k_plan_keys  sort keys (descending predicted cost) and split counts.
 // Labels are log1p of the work each root's search measured (adjacency
@@ -31,6 +34,7 @@ struct tm_model {
     float *master = nullptr;   // TM_MODEL_PARAMS fp32
     __half *half = nullptr;    // fp16 copy used by the kernels
     float *m = nullptr, *v = nullptr, *grad = nullptr;
+    float *part = nullptr;     // kGradSlots x (TM_MODEL_PARAMS + 1): per-block gradient and loss sums
     float *norm = nullptr;     // 16: feature mean[8], inverse std[8]
     float *acc = nullptr;      // loss accumulator
     int64_t step = 0;
@@ -45,6 +49,9 @@ constexpr int oW1 = 0, oB1 = oW1 + kH * kIn, oW2 = oB1 + kH, oB2 = oW2 + kH * kH
 constexpr int kParams = oB3 + 1;
 static_assert(kParams == TM_MODEL_PARAMS, "parameter count");
 constexpr int kGradThreads = 64;
+constexpr int kGradSlots = 64;      // blocks of a gradient launch, each with its own partial sums
+constexpr int kPart = kParams + 1;  // one slot: the gradient, then the loss
+constexpr int kNormThreads = 256;
 
 __device__ __forceinline__ float h2f(__half x) { return __half2float(x); }
 
@@ -101,28 +108,35 @@ __global__ void k_features(DevGraph g, const int32_t *roots, int64_t n, int64_t 
 }
 
 // sums[f] and sums[8 + f] of feature f and its square
-__global__ void k_feat_sums(const float *X, int64_t n, float *sums) {
-    __shared__ float s[2 * kIn];
-    if (threadIdx.x < 2 * kIn) s[threadIdx.x] = 0;
-    __syncthreads();
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n)
+// Feature mean and inverse standard deviation over n samples, one block:
+// each thread sums a fixed stride of samples, then a fixed-order tree adds
+// the threads' sums (FP64), so the result does not depend on scheduling.
+__global__ void __launch_bounds__(kNormThreads) k_feat_norm(const float *X, int64_t n, float *norm) {
+    __shared__ double s[2 * kIn][kNormThreads];
+    double a[2 * kIn];
+#pragma unroll
+    for (int f = 0; f < 2 * kIn; f++) a[f] = 0.0;
+    for (int64_t i = threadIdx.x; i < n; i += kNormThreads)
+#pragma unroll
         for (int f = 0; f < kIn; f++) {
-            float x = X[i * kIn + f];
-            atomicAdd(&s[f], x);
-            atomicAdd(&s[kIn + f], x * x);
+            const double x = X[i * kIn + f];
+            a[f] += x;
+            a[kIn + f] += x * x;
         }
+#pragma unroll
+    for (int f = 0; f < 2 * kIn; f++) s[f][threadIdx.x] = a[f];
     __syncthreads();
-    if (threadIdx.x < 2 * kIn) atomicAdd(&sums[threadIdx.x], s[threadIdx.x]);
-}
-
-__global__ void k_feat_norm(const float *sums, int64_t n, float *norm) {
-    int f = threadIdx.x;
+    for (int h = kNormThreads / 2; h > 0; h >>= 1) {
+        if ((int)threadIdx.x < h)
+            for (int f = 0; f < 2 * kIn; f++) s[f][threadIdx.x] += s[f][threadIdx.x + h];
+        __syncthreads();
+    }
+    const int f = threadIdx.x;
     if (f >= kIn) return;
-    float mean = sums[f] / (float)n;
-    float var = fmaxf(sums[kIn + f] / (float)n - mean * mean, 0.f);
-    norm[f] = mean;
-    norm[kIn + f] = var > 1e-8f ? rsqrtf(var) : 1.f;
+    const double mean = s[f][0] / (double)n;
+    const double var = fmax(s[kIn + f][0] / (double)n - mean * mean, 0.0);
+    norm[f] = (float)mean;
+    norm[kIn + f] = var > 1e-8 ? (float)(1.0 / sqrt(var)) : 1.f;
 }
 
 __device__ __forceinline__ void load_weights(const __half *W, __half *sW) {
@@ -158,100 +172,126 @@ __global__ void k_mlp_fwd(const __half *W, const float *norm, const float *X, in
     Y[i] = y;
 }
 
-// Gradient of sum over the minibatch of (y - t)^2 / n_total, added into grad.
+// Gradient of sum over the minibatch of (y - t)^2 * inv_n, and that loss,
+// into per-block partial sums: block b takes the 64-sample tiles b,
+// b + gridDim.x, ... in that order and owns part[b * kPart .. + kPart)
+// (every parameter's sum belongs to one thread of the block, the loss to
+// thread 0), so nothing is added atomically.
 __global__ void __launch_bounds__(kGradThreads) k_mlp_grad(const __half *W, const float *norm, const float *X,
-                                                           const float *T, int64_t n, float inv_n, float *grad,
-                                                           float *loss) {
+                                                           const float *T, int64_t n, float inv_n, float *part) {
     __shared__ __half sW[kParams];
     __shared__ float sN[2 * kIn];
     __shared__ float sX[kGradThreads][kIn];
     __shared__ float sH1[kGradThreads][kH + 1];   // h1, later dz1
     __shared__ float sH2[kGradThreads][kH + 1];   // h2, later dz2
     __shared__ float sDy[kGradThreads];
+    __shared__ float sE[kGradThreads];            // squared error * inv_n
     load_weights(W, sW);
     if (threadIdx.x < 2 * kIn) sN[threadIdx.x] = norm[threadIdx.x];
     __syncthreads();
     const int s = threadIdx.x;
-    const int64_t i = (int64_t)blockIdx.x * kGradThreads + s;
-    const bool live = i < n;
-    // forward
+    float *slot = part + (int64_t)blockIdx.x * kPart;
+    const int64_t n_tiles = (n + kGradThreads - 1) / kGradThreads;
+    for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+        const bool first = tile == blockIdx.x;
+        auto put = [&](int idx, float g) { slot[idx] = first ? g : slot[idx] + g; };
+        const int64_t i = tile * kGradThreads + s;
+        const bool live = i < n;
+        // forward
 #pragma unroll
-    for (int f = 0; f < kIn; f++) sX[s][f] = live ? (X[i * kIn + f] - sN[f]) * sN[kIn + f] : 0.f;
-    for (int j = 0; j < kH; j++) {
-        float z = h2f(sW[oB1 + j]);
+        for (int f = 0; f < kIn; f++) sX[s][f] = live ? (X[i * kIn + f] - sN[f]) * sN[kIn + f] : 0.f;
+        for (int j = 0; j < kH; j++) {
+            float z = h2f(sW[oB1 + j]);
 #pragma unroll
-        for (int f = 0; f < kIn; f++) z = fmaf(h2f(sW[oW1 + j * kIn + f]), sX[s][f], z);
-        sH1[s][j] = live ? fmaxf(z, 0.f) : 0.f;
-    }
-    float y = h2f(sW[oB3]);
-    for (int j = 0; j < kH; j++) {
-        float z = h2f(sW[oB2 + j]);
-        for (int q = 0; q < kH; q++) z = fmaf(h2f(sW[oW2 + j * kH + q]), sH1[s][q], z);
-        const float h = live ? fmaxf(z, 0.f) : 0.f;
-        sH2[s][j] = h;
-        y = fmaf(h2f(sW[oW3 + j]), h, y);
-    }
-    const float err = live ? y - T[i] : 0.f;
-    sDy[s] = 2.f * err * inv_n;
-    atomicAdd(loss, err * err * inv_n);
-    __syncthreads();
-    // output layer: dW3[j] = sum_s dy_s h2_s[j]
-    {
-        const int j = s;
-        float g = 0.f;
-        for (int q = 0; q < kGradThreads; q++) g = fmaf(sDy[q], sH2[q][j], g);
-        atomicAdd(&grad[oW3 + j], g);
-        if (s == 0) {
-            float b = 0.f;
-            for (int q = 0; q < kGradThreads; q++) b += sDy[q];
-            atomicAdd(&grad[oB3], b);
+            for (int f = 0; f < kIn; f++) z = fmaf(h2f(sW[oW1 + j * kIn + f]), sX[s][f], z);
+            sH1[s][j] = live ? fmaxf(z, 0.f) : 0.f;
         }
-    }
-    __syncthreads();
-    // dz2 = dy * W3 where h2 > 0 (overwrites h2 of this sample)
-    for (int j = 0; j < kH; j++) sH2[s][j] = (sH2[s][j] > 0.f) ? sDy[s] * h2f(sW[oW3 + j]) : 0.f;
-    __syncthreads();
-    // dW2[j][q] = sum_s dz2_s[j] h1_s[q]; db2[j] = sum_s dz2_s[j]
-    {
-        const int j = s;
-        float b = 0.f;
-        for (int q = 0; q < kGradThreads; q++) b += sH2[q][j];
-        atomicAdd(&grad[oB2 + j], b);
-        for (int q = 0; q < kH; q++) {
+        float y = h2f(sW[oB3]);
+        for (int j = 0; j < kH; j++) {
+            float z = h2f(sW[oB2 + j]);
+            for (int q = 0; q < kH; q++) z = fmaf(h2f(sW[oW2 + j * kH + q]), sH1[s][q], z);
+            const float h = live ? fmaxf(z, 0.f) : 0.f;
+            sH2[s][j] = h;
+            y = fmaf(h2f(sW[oW3 + j]), h, y);
+        }
+        const float err = live ? y - T[i] : 0.f;
+        sDy[s] = 2.f * err * inv_n;
+        sE[s] = err * err * inv_n;
+        __syncthreads();
+        // output layer: dW3[j] = sum_s dy_s h2_s[j]; the loss
+        {
+            const int j = s;
             float g = 0.f;
-            for (int r = 0; r < kGradThreads; r++) g = fmaf(sH2[r][j], sH1[r][q], g);
-            atomicAdd(&grad[oW2 + j * kH + q], g);
+            for (int q = 0; q < kGradThreads; q++) g = fmaf(sDy[q], sH2[q][j], g);
+            put(oW3 + j, g);
+            if (s == 0) {
+                float b = 0.f, l = 0.f;
+                for (int q = 0; q < kGradThreads; q++) {
+                    b += sDy[q];
+                    l += sE[q];
+                }
+                put(oB3, b);
+                put(kParams, l);
+            }
         }
-    }
-    __syncthreads();
-    // dz1[q] = sum_j W2[j][q] dz2[j] where h1 > 0 (overwrites h1 of this sample)
-    {
-        float d[kH];
-        for (int q = 0; q < kH; q++) {
-            float z = 0.f;
-            for (int j = 0; j < kH; j++) z = fmaf(h2f(sW[oW2 + j * kH + q]), sH2[s][j], z);
-            d[q] = z;
+        __syncthreads();
+        // dz2 = dy * W3 where h2 > 0 (overwrites h2 of this sample)
+        for (int j = 0; j < kH; j++) sH2[s][j] = (sH2[s][j] > 0.f) ? sDy[s] * h2f(sW[oW3 + j]) : 0.f;
+        __syncthreads();
+        // dW2[j][q] = sum_s dz2_s[j] h1_s[q]; db2[j] = sum_s dz2_s[j]
+        {
+            const int j = s;
+            float b = 0.f;
+            for (int q = 0; q < kGradThreads; q++) b += sH2[q][j];
+            put(oB2 + j, b);
+            for (int q = 0; q < kH; q++) {
+                float g = 0.f;
+                for (int r = 0; r < kGradThreads; r++) g = fmaf(sH2[r][j], sH1[r][q], g);
+                put(oW2 + j * kH + q, g);
+            }
         }
-        for (int q = 0; q < kH; q++) sH1[s][q] = (sH1[s][q] > 0.f) ? d[q] : 0.f;
-    }
-    __syncthreads();
-    // dW1[q][f] = sum_s dz1_s[q] x_s[f]; db1[q] = sum_s dz1_s[q]
-    {
-        const int q = s;
-        float b = 0.f;
-        float g[kIn];
-#pragma unroll
-        for (int f = 0; f < kIn; f++) g[f] = 0.f;
-        for (int r = 0; r < kGradThreads; r++) {
-            const float d = sH1[r][q];
-            b += d;
-#pragma unroll
-            for (int f = 0; f < kIn; f++) g[f] = fmaf(d, sX[r][f], g[f]);
+        __syncthreads();
+        // dz1[q] = sum_j W2[j][q] dz2[j] where h1 > 0 (overwrites h1 of this sample)
+        {
+            float d[kH];
+            for (int q = 0; q < kH; q++) {
+                float z = 0.f;
+                for (int j = 0; j < kH; j++) z = fmaf(h2f(sW[oW2 + j * kH + q]), sH2[s][j], z);
+                d[q] = z;
+            }
+            for (int q = 0; q < kH; q++) sH1[s][q] = (sH1[s][q] > 0.f) ? d[q] : 0.f;
         }
-        atomicAdd(&grad[oB1 + q], b);
+        __syncthreads();
+        // dW1[q][f] = sum_s dz1_s[q] x_s[f]; db1[q] = sum_s dz1_s[q]
+        {
+            const int q = s;
+            float b = 0.f;
+            float g[kIn];
 #pragma unroll
-        for (int f = 0; f < kIn; f++) atomicAdd(&grad[oW1 + q * kIn + f], g[f]);
+            for (int f = 0; f < kIn; f++) g[f] = 0.f;
+            for (int r = 0; r < kGradThreads; r++) {
+                const float d = sH1[r][q];
+                b += d;
+#pragma unroll
+                for (int f = 0; f < kIn; f++) g[f] = fmaf(d, sX[r][f], g[f]);
+            }
+            put(oB1 + q, b);
+#pragma unroll
+            for (int f = 0; f < kIn; f++) put(oW1 + q * kIn + f, g[f]);
+        }
+        __syncthreads();                 // the next tile overwrites the shared arrays
     }
+}
+
+// grad[i] = the blocks' partial sums of parameter i, added in block order;
+// the loss likewise, stored (add == 0) or added (add == 1) to *loss.
+__global__ void k_grad_sum(const float *part, int n_blocks, float *grad, float *loss, int add) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= kPart) return;
+    float v = 0.f;
+    for (int b = 0; b < n_blocks; b++) v += part[(int64_t)b * kPart + i];
+    if (i < kParams) grad[i] = v;
+    else *loss = add ? *loss + v : v;
 }
 
 __global__ void k_adam(float *w, __half *wh, float *m, float *v, const float *g, int n, float lr, float b1, float b2,
@@ -355,6 +395,7 @@ int tm_model_create(uint64_t seed, tm_model **out) {
     if (e == cudaSuccess) e = cudaMalloc(&m->m, sizeof(float) * kParams);
     if (e == cudaSuccess) e = cudaMalloc(&m->v, sizeof(float) * kParams);
     if (e == cudaSuccess) e = cudaMalloc(&m->grad, sizeof(float) * kParams);
+    if (e == cudaSuccess) e = cudaMalloc(&m->part, sizeof(float) * kGradSlots * kPart);
     if (e == cudaSuccess) e = cudaMalloc(&m->norm, sizeof(float) * 2 * kIn);
     if (e == cudaSuccess) e = cudaMalloc(&m->acc, sizeof(float) * 32);
     std::vector<float> norm(2 * kIn, 0.f);
@@ -383,6 +424,7 @@ int tm_model_free(tm_model *m) {
     cudaFree(m->m);
     cudaFree(m->v);
     cudaFree(m->grad);
+    cudaFree(m->part);
     cudaFree(m->norm);
     cudaFree(m->acc);
     delete m;
@@ -411,9 +453,7 @@ int tm_model_set_params(tm_model *m, const float *params, const float *norm) {
 int tm_model_fit_norm(tm_model *m, const float *feats, int64_t n, void *stream) {
     if (!m || !feats || n <= 0) { set_error("tm_model_fit_norm: bad argument"); return TM_EINVAL; }
     cudaStream_t s = (cudaStream_t)stream;
-    TM_CUDA_TRY(cudaMemsetAsync(m->acc, 0, sizeof(float) * 2 * kIn, s));
-    k_feat_sums<<<grid(n), 256, 0, s>>>(feats, n, m->acc);
-    k_feat_norm<<<1, 32, 0, s>>>(m->acc, n, m->norm);
+    k_feat_norm<<<1, kNormThreads, 0, s>>>(feats, n, m->norm);
     TM_CUDA_TRY(cudaGetLastError());
     return TM_OK;
 }
@@ -426,15 +466,26 @@ int tm_model_predict(const tm_model *m, const float *feats, int64_t n, float *ou
     return TM_OK;
 }
 
+namespace {
+// m->grad = the gradient of the mean squared error over n samples; the loss
+// stored (add == 0) or added (add == 1) to *loss.  Reproducible: per-block
+// partial sums in fixed slots, added in block order.
+int gradient(const tm_model *m, const float *feats, const float *labels, int64_t n, float *loss, int add,
+             cudaStream_t s) {
+    const int64_t n_tiles = (n + kGradThreads - 1) / kGradThreads;
+    const int blocks = (int)std::min<int64_t>(n_tiles, kGradSlots);
+    k_mlp_grad<<<blocks, kGradThreads, 0, s>>>(m->half, m->norm, feats, labels, n, 1.f / (float)n, m->part);
+    k_grad_sum<<<grid(kPart), 256, 0, s>>>(m->part, blocks, m->grad, loss, add);
+    TM_CUDA_TRY(cudaGetLastError());
+    return TM_OK;
+}
+}  // namespace
+
 int tm_model_loss_grad(const tm_model *m, const float *feats, const float *labels, int64_t n, float *loss,
                        float *grad, void *stream) {
     if (!m || n <= 0 || !feats || !labels) { set_error("tm_model_loss_grad: bad argument"); return TM_EINVAL; }
     cudaStream_t s = (cudaStream_t)stream;
-    TM_CUDA_TRY(cudaMemsetAsync(m->grad, 0, sizeof(float) * kParams, s));
-    TM_CUDA_TRY(cudaMemsetAsync(m->acc, 0, sizeof(float), s));
-    k_mlp_grad<<<grid(n, kGradThreads), kGradThreads, 0, s>>>(m->half, m->norm, feats, labels, n, 1.f / (float)n,
-                                                               m->grad, m->acc);
-    TM_CUDA_TRY(cudaGetLastError());
+    TM_TRY(gradient(m, feats, labels, n, m->acc, 0, s));
     if (loss) TM_CUDA_TRY(cudaMemcpyAsync(loss, m->acc, sizeof(float), cudaMemcpyDeviceToHost, s));
     if (grad) TM_CUDA_TRY(cudaMemcpyAsync(grad, m->grad, sizeof(float) * kParams, cudaMemcpyDeviceToHost, s));
     TM_CUDA_TRY(cudaStreamSynchronize(s));
@@ -453,11 +504,7 @@ int tm_model_train(tm_model *m, const float *feats, const float *labels, int64_t
         TM_CUDA_TRY(cudaMemsetAsync(m->acc + 1, 0, sizeof(float), s));
         for (int64_t lo = 0; lo < n; lo += batch) {
             const int64_t nb = std::min<int64_t>(batch, n - lo);
-            TM_CUDA_TRY(cudaMemsetAsync(m->grad, 0, sizeof(float) * kParams, s));
-            TM_CUDA_TRY(cudaMemsetAsync(m->acc, 0, sizeof(float), s));
-            k_mlp_grad<<<grid(nb, kGradThreads), kGradThreads, 0, s>>>(m->half, m->norm, feats + lo * kIn,
-                                                                        labels + lo, nb, 1.f / (float)nb, m->grad,
-                                                                        m->acc + 1);
+            TM_TRY(gradient(m, feats + lo * kIn, labels + lo, nb, m->acc + 1, 1, s));
             m->step++;
             const float c1 = 1.f - std::pow(b1, (float)m->step), c2 = 1.f - std::pow(b2, (float)m->step);
             k_adam<<<grid(kParams), 256, 0, s>>>(m->master, m->half, m->m, m->v, m->grad, kParams, lr, b1, b2, eps,

@@ -98,6 +98,40 @@ def test_forward_and_gradient_match_float64_reference():
     assert np.max(np.abs(g - g_ref)) <= 2e-4 * scale
 
 
+def test_gradient_over_many_tiles_and_reproducible_training():
+    """More 64-sample tiles than gradient blocks (each block takes several,
+    the last one ragged) against the float64 reference; and the sums have no
+    floating-point atomics, so two trainings from one seed on the same data
+    end with the same parameters and losses, bit for bit."""
+    import torch
+    rng = np.random.default_rng(9)
+    n = 64 * 64 * 2 + 37                 # 129 tiles over 64 blocks
+    X = rng.normal(1, 2, (n, 8)).astype(np.float32)
+    T = (X[:, 0] * X[:, 1] + rng.normal(3, 1, n)).astype(np.float32)
+    dX, dT = torch.from_numpy(X).cuda(), torch.from_numpy(T).cuda()
+    m = tmotif.Model(seed=5)
+    m.fit_norm(dX)
+    torch.cuda.synchronize()
+    theta, norm = _half_theta(m)
+    assert np.allclose(norm[:8], X.mean(0), rtol=1e-4, atol=1e-4)
+    assert np.allclose(norm[8:], 1 / X.std(0), rtol=1e-3)
+    loss, g = m.loss_grad(dX, dT)
+    loss_ref, g_ref = mlp.loss_grad(theta, _std(X.astype(np.float64), norm), T.astype(np.float64))
+    assert abs(loss - loss_ref) <= 1e-4 * abs(loss_ref) + 1e-5
+    assert np.max(np.abs(g - g_ref)) <= 2e-4 * np.abs(g_ref).max()
+    runs = []
+    for _ in range(2):
+        mm = tmotif.Model(seed=5)
+        mm.fit_norm(dX)
+        hist = mm.train(dX, dT, epochs=6, batch=5000, lr=3e-3)
+        w, nrm = mm.params()
+        runs.append((w, nrm, np.asarray(hist), mm.loss_grad(dX, dT)[0]))
+        mm.close()
+    (w0, n0, h0, l0), (w1, n1, h1, l1) = runs
+    assert np.array_equal(w0, w1) and np.array_equal(n0, n1) and np.array_equal(h0, h1) and l0 == l1
+    assert h0[-1] < h0[0]
+
+
 def test_training_reduces_error():
     import torch
     rng = np.random.default_rng(8)
