@@ -35,8 +35,11 @@ def test_generated_programs_compile_for_sm103a():
         assert info["kernels"] == 1 and info["compiled"] == 1
         assert 0 < info["registers"] <= 80          # __launch_bounds__(256, 3)
         assert info["static_smem"] > 0
-    # the mid tree: depth 4 and 5 vertices size the per-warp state
+    # the mid tree: depth 4 and 5 vertices size the per-warp state, and the
+    # kernel spills at most a few words (the table-driven kernel: 36 B of
+    # spill stores at the same 80 registers)
     assert out[0]["static_smem"] < 39488
+    assert all(0 <= info["local_bytes"] <= 16 for info in out)
     # a check attaches nothing to the tree
     assert all(t.info()["specialized"] == 0 for t in trees)
 
