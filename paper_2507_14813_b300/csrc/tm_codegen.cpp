@@ -336,6 +336,8 @@ int tree_compile(tm_tree *tr, uint32_t flags, tm_compile_info *info) {
     for (auto &t : pool) t.join();
     for (int i = 0; i < n_prog; i++)
         if (rc[i] != TM_OK) {
+            if (check)                   // a check's records of the programs that did compile
+                for (const SpecKernel *k : ks) delete k;
             set_error(err[i]);
             return rc[i];
         }
